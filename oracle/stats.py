@@ -1,0 +1,130 @@
+"""Ensemble statistics of an approximate statistical solution (oracle).
+
+TEST INFRASTRUCTURE ONLY.
+
+Algorithm 1 (section 2.1) approximates the statistical solution by the
+empirical measure (1/M) sum_i delta_{u_i(t)} of M Monte Carlo samples; the
+writers of section 2.4 reduce it to observables.  The paper prints no
+formulas for them; the definitions used (both here and in the library) are:
+
+* mean field            m_i(x)    = (1/M) sum_m u_{m,i}(x)        on the N^3 grid
+* second moments        E[u_i u_j](x) = (1/M) sum_m u_{m,i} u_{m,j}  (i <= j,
+                        order 00 01 02 11 12 22)
+* pointwise variance    v_i(x)    = (1/(M-1)) sum_m (u_{m,i} - m_i)^2
+* energy spectrum       E(K)      = 1/2 sum_{k : round(|k|) = K} |u_hat_k|^2
+                        (full spectrum, K = 0 .. N-1), mean over samples
+* structure function    S2(r)     = (1/3) sum_d <|u(x + r e_d) - u(x)|^2>_x
+                                  = (1/3) sum_d sum_k 2 |u_hat_k|^2 (1 - cos(kappa_d r)),
+                        r = j L / N, j = 1 .. N/2
+* Monte Carlo standard error of a sample mean: sqrt(var / M).
+
+Sample sets are merged with the pairwise formula of Chan, Golub and LeVeque
+(count, mean, sum of squared deviations).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .solver import half_weights, to_physical, wavenumbers
+
+PAIRS = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def physical_on_grid(uhat: np.ndarray) -> np.ndarray:
+    """u at the N^3 grid points (no padding)."""
+    return to_physical(uhat, uhat.shape[-2])
+
+
+def shell_index(N: int) -> np.ndarray:
+    """round(|k|) on the D1 grid, as int."""
+    kx, ky, kz = wavenumbers(N)
+    k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
+    return np.floor(np.sqrt(k2) + 0.5).astype(np.int64)
+
+
+def energy_spectrum(uhat: np.ndarray) -> np.ndarray:
+    N = uhat.shape[-2]
+    e = 0.5 * np.sum(np.abs(uhat) ** 2, axis=0) * half_weights(N)
+    sh = np.broadcast_to(shell_index(N), e.shape)
+    return np.bincount(sh.ravel(), weights=e.ravel(), minlength=N)[:N]
+
+
+def structure_function_spectral(uhat: np.ndarray, L: float) -> np.ndarray:
+    N = uhat.shape[-2]
+    kx, ky, kz = wavenumbers(N)
+    e = np.sum(np.abs(uhat) ** 2, axis=0) * half_weights(N)
+    out = np.zeros(N // 2)
+    for j in range(1, N // 2 + 1):
+        r = j * L / N
+        acc = 0.0
+        for kd in (kx, ky, kz):
+            kap = (2 * math.pi / L) * kd
+            acc += np.sum(e * 2.0 * (1.0 - np.cos(kap * r)))
+        out[j - 1] = acc / 3.0
+    return out
+
+
+def structure_function_brute(u: np.ndarray) -> np.ndarray:
+    """S2 from grid values by shifting whole grid points (r = j L / N)."""
+    N = u.shape[-1]
+    out = np.zeros(N // 2)
+    for j in range(1, N // 2 + 1):
+        acc = 0.0
+        for ax in (1, 2, 3):
+            acc += np.mean(np.sum((np.roll(u, -j, axis=ax) - u) ** 2, axis=0))
+        out[j - 1] = acc / 3.0
+    return out
+
+
+def mean_and_stderr(samples: np.ndarray):
+    """Sample mean and Monte Carlo standard error along axis 0."""
+    M = samples.shape[0]
+    mean = samples.mean(axis=0)
+    if M < 2:
+        return mean, np.zeros_like(mean)
+    var = samples.var(axis=0, ddof=1)
+    return mean, np.sqrt(var / M)
+
+
+def ensemble_stats(uhats: np.ndarray, L: float) -> dict:
+    """All writer statistics of an ensemble given as (M, 3, N, N, N/2+1)."""
+    M = uhats.shape[0]
+    N = uhats.shape[-2]
+    phys = np.stack([physical_on_grid(u) for u in uhats])           # (M,3,N,N,N)
+    mean = phys.mean(axis=0)
+    second = np.stack([(phys[:, i] * phys[:, j]).mean(axis=0) for i, j in PAIRS])
+    var = phys.var(axis=0, ddof=1) if M > 1 else np.zeros_like(mean)
+    spec = np.stack([energy_spectrum(u) for u in uhats])
+    s2 = np.stack([structure_function_spectral(u, L) for u in uhats])
+    en = spec.sum(axis=1)
+    spec_m, spec_se = mean_and_stderr(spec)
+    s2_m, s2_se = mean_and_stderr(s2)
+    en_m, en_se = mean_and_stderr(en)
+    return dict(M=M, N=N, mean=mean, second=second, var=var,
+                spectrum=spec_m, spectrum_stderr=spec_se,
+                s2=s2_m, s2_stderr=s2_se,
+                energy=float(en_m), energy_stderr=float(en_se))
+
+
+def chan_merge(a, b):
+    """Merge two (count, mean, M2) triples; M2 = sum of squared deviations."""
+    na, ma, qa = a
+    nb, mb, qb = b
+    n = na + nb
+    if n == 0:
+        return (0, ma, qa)
+    d = mb - ma
+    return (n, ma + d * (nb / n), qa + qb + d * d * (na * nb / n))
+
+
+def welford(samples: np.ndarray):
+    """(count, mean, M2) of samples along axis 0, one sample at a time."""
+    n, mean, m2 = 0, np.zeros_like(samples[0], dtype=np.float64), np.zeros_like(samples[0], dtype=np.float64)
+    for x in samples:
+        n += 1
+        d = x - mean
+        mean = mean + d / n
+        m2 = m2 + d * (x - mean)
+    return n, mean, m2

@@ -1,0 +1,147 @@
+"""Pins for the oracle's statistics (Parseval, brute-force structure function,
+zero variance, Chan merge) and for its discrete adjoint (dot-product tests,
+central finite differences, the Beltrami closed form)."""
+import math
+
+import numpy as np
+import pytest
+
+import ns3d_inputs as I
+from oracle import adjoint as A
+from oracle import solver as S
+from oracle import stats as T
+
+TWO_PI = 2 * math.pi
+
+
+# --------------------------------------------------------------------------- statistics
+
+def test_spectrum_sums_to_energy():
+    uh = I.random_spectrum(16, seed=3, k0=3.0)
+    assert abs(T.energy_spectrum(uh).sum() - S.energy(uh)) < 1e-15
+    tg = T.energy_spectrum(I.taylor_green(16))
+    assert abs(tg[2] - 0.125) < 1e-15 and abs(tg.sum() - 0.125) < 1e-15   # round(sqrt 3) = 2
+
+
+@pytest.mark.parametrize("N,L", [(8, TWO_PI), (16, TWO_PI), (12, 1.0)])
+def test_structure_function_spectral_equals_brute_force(N, L):
+    uh = I.random_spectrum(N, seed=N, k0=2.0)
+    u = T.physical_on_grid(uh)
+    assert np.allclose(T.structure_function_spectral(uh, L), T.structure_function_brute(u),
+                       rtol=1e-12, atol=1e-15)
+
+
+def test_identical_samples_have_zero_variance_and_exact_moments():
+    uh = I.random_spectrum(8, seed=1)
+    st = T.ensemble_stats(np.stack([uh] * 4), TWO_PI)
+    u = T.physical_on_grid(uh)
+    assert np.max(np.abs(st["var"])) < 1e-28
+    assert np.max(np.abs(st["spectrum_stderr"])) < 1e-15
+    assert np.allclose(st["mean"], u, atol=1e-15)
+    assert np.allclose(st["second"][1], u[0] * u[1], atol=1e-15)
+
+
+def test_chan_merge_equals_two_pass():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((37, 5)) * 3 + 1
+    a = T.welford(x[:20])
+    b = T.welford(x[20:])
+    n, m, q = T.chan_merge(a, b)
+    assert n == 37
+    assert np.allclose(m, x.mean(0), rtol=1e-14)
+    assert np.allclose(q / (n - 1), x.var(0, ddof=1), rtol=1e-13)
+
+
+def test_mean_and_stderr_of_known_samples():
+    s = np.array([[1.0], [3.0], [5.0]])
+    m, se = T.mean_and_stderr(s)
+    assert m[0] == 3.0 and abs(se[0] - math.sqrt(4.0 / 3.0)) < 1e-15
+
+
+# --------------------------------------------------------------------------- adjoint
+
+def _rand_field(N, seed, div_free=True):
+    if div_free:
+        return I.random_spectrum(N, seed=seed, k0=2.5, energy=0.3)
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((3, N, N, N))
+    return I.coefficients_of(u)
+
+
+@pytest.mark.parametrize("div_free", [True, False])
+def test_adjoint_rhs_dot_product(div_free):
+    N = 12
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u = I.random_spectrum(N, seed=1, k0=2.5)
+    du = _rand_field(N, 2, div_free)
+    w = _rand_field(N, 3, div_free)
+    lhs = S.inner(w, A.tangent_rhs(u, du, prm))
+    rhs = S.inner(A.adjoint_rhs(u, w, prm), du)
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+def test_tangent_rhs_matches_finite_difference():
+    N = 12
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u = I.random_spectrum(N, seed=1, k0=2.5)
+    du = _rand_field(N, 2)
+    h = 1e-5
+    fd = (S.rhs(u + h * du, prm) - S.rhs(u - h * du, prm)) / (2 * h)
+    tl = A.tangent_rhs(u, du, prm)
+    assert np.linalg.norm((fd - tl).ravel()) < 1e-9 * np.linalg.norm(tl.ravel())
+
+
+def test_rk3_adjoint_step_dot_product():
+    N = 12
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u = I.random_spectrum(N, seed=5, k0=2.5)
+    du = _rand_field(N, 6, False)
+    lam = _rand_field(N, 7, False)
+    dt = 0.05
+    lhs = S.inner(lam, A.rk3_tangent_step(u, du, dt, prm))
+    rhs = S.inner(A.rk3_adjoint_step(u, lam, dt, prm), du)
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+def test_band_energy_gradient_finite_differences():
+    N = 12
+    prm = S.Params(nu=0.01, eps0=1.0)
+    dt, n = 0.05, 4
+    u0 = I.random_spectrum(N, seed=8, k0=2.5)
+    g = A.grad_band_energy(u0, prm, n, dt, 2.0, 4.0, checkpoint_every=3)
+
+    def J(u):
+        un, _, _ = S.integrate(u, prm.with_(dt_fixed=dt), n)
+        return A.band_energy(un, 2.0, 4.0)
+
+    for seed in (1, 2):
+        v = I.random_spectrum(N, seed=100 + seed, k0=2.5, energy=0.5)
+        h = 1e-4
+        fd = (J(u0 + h * v) - J(u0 - h * v)) / (2 * h)
+        assert abs(fd - S.inner(g, v)) < 2e-8 * abs(fd)
+
+
+def test_checkpointing_does_not_change_gradient():
+    N = 8
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u0 = I.random_spectrum(N, seed=2, k0=2.0)
+    g1 = A.grad_band_energy(u0, prm, 5, 0.05, 1.0, 3.0, checkpoint_every=0)
+    g2 = A.grad_band_energy(u0, prm, 5, 0.05, 1.0, 3.0, checkpoint_every=2)
+    assert np.array_equal(g1, g2)
+
+
+def test_beltrami_gradient_closed_form():
+    """For a Beltrami field on the shell |k| = K the nonlinear term and its
+    adjoint act only through gradients: the divergence-free part of dJ/du0 is
+    r(-lambda_K dt)^(2n) u0 when K is in the band, 0 otherwise."""
+    N = 16
+    prm = S.Params(nu=0.05, s=1.5, theta=0.25, eps0=2.0)
+    u0 = I.single_shell_beltrami(N, K=3)
+    lamK = 0.05 * 9 + 2.0 / 256.0 * 27.0 * (1.0 - (4.0 / 9.0) ** 4)
+    dt, n = 0.05, 3
+    r = 1 - lamK * dt + (lamK * dt) ** 2 / 2 - (lamK * dt) ** 3 / 6
+    g = A.grad_band_energy(u0, prm, n, dt, 2.5, 3.5)
+    pg = S.leray(g, TWO_PI)
+    assert np.linalg.norm((pg - r ** (2 * n) * u0).ravel()) < 1e-13 * np.linalg.norm(u0.ravel())
+    g_out = A.grad_band_energy(u0, prm, n, dt, 4.0, 6.0)
+    assert np.max(np.abs(S.leray(g_out, TWO_PI))) < 1e-15
