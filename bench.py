@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of the SSP-RK3 pseudo-spectral step on GB300.
+
+Metric: grid-point steps per second, sum over members of N^3 x completed RK3
+steps / second (one step = three evaluations of Algorithm 2 + the RK3
+combines).  Default workload: one 256^3 sample per GPU in FP32 (padded grid
+384^3), seeded random divergence-free initial data with E(k) ~ k^4
+exp(-2 (k/4)^2) and energy 0.5, the hyper-viscosity for N (s = 1.5,
+theta = 1/2, eps0 = m_N coefficient = 1), CFL 0.5.  Inputs live in HBM when
+the timed region starts; every step streams about 18 GB, far above the
+126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank advances its own sample (weak scaling: the Monte
+Carlo ensemble shards with no data-path collective).  Rank 0 prints one JSON
+line.  ``--impl reference`` times the CPU oracle instead (the paper has no
+code to run): each step is one RK3 step of the oracle at 32^3.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt-steps/s at 256^3 (plain vs batched FP32 ensemble), % of HBM roofline"
+UNIT = "grid-pt-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--members", type=int, default=1, help="members per GPU at N")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- byte model
+
+def kernel_bytes(N: int, P: int, esz: int, members: int):
+    """Algorithmic bytes per launch of each kernel kind (compulsory reads and
+    writes of its input and output arrays; complex elements of esz bytes)."""
+    h = N // 2
+    U = 3 * N * N * h
+    A = 3 * P * N * h
+    Bq = 3 * P * h * P
+    Cq = 6 * P * h * P
+    Dq = 6 * P * N * h
+    Bh = 6 * N * N * h
+    per = {
+        "inverse_x": U + A,
+        "inverse_y": A + Bq,
+        "zpass": Bq + Cq,
+        "forward_y": Cq + Dq,
+        "forward_x": Dq + Bh,
+        "spectral": Bh + U + U + (2 * U) / 3.0,   # stages 2, 3 also read the stage state
+    }
+    return {k: v * esz * members for k, v in per.items()}
+
+
+KINDS = ["inverse_x", "inverse_y", "zpass", "forward_y", "forward_x", "spectral"]
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_sample_seconds(N: int, steps: int = 1) -> float:
+    """Wall seconds of `steps` oracle RK3 steps at N^3 in a fresh single-threaded process."""
+    code = (
+        "import time, sys; sys.path.insert(0, %r)\n"
+        "import ns3d_inputs as I\n"
+        "from oracle import solver as S\n"
+        "u = I.random_spectrum(%d, seed=20240001)\n"
+        "prm = S.Params(eps0=1.0, cfl=0.5)\n"
+        "S.rk3_step(u, prm)\n"
+        "t = time.perf_counter()\n"
+        "S.integrate(u, prm, %d)\n"
+        "print(time.perf_counter() - t)\n" % (ROOT, N, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, text=True,
+                         check=True)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    N = 64
+    sec = oracle_sample_seconds(N, 1)
+    return {"value": N ** 3 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one SSP-RK3 step of the FP64 numpy oracle at {N}^3 (P = 96), same "
+                      f"initial-data family and parameters, single thread; {sec:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    N = 32
+    for _ in range(args.warmup):
+        oracle_sample_seconds(N, 1)
+    per = [oracle_sample_seconds(N, 1) for _ in range(args.steps)]
+    tot = sum(per)
+    value = N ** 3 * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.N}^3 random-spectrum sample per GPU, CFL 0.5, s=1.5",
+                   "N": args.N, "members_per_gpu": args.members, "l2": "inputs > L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step is one SSP-RK3 step of the FP64 numpy oracle at {N}^3 "
+                                   "(the paper publishes no code to run), single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import ns3d_inputs as I
+    from paper_2401_09843_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    N, M = args.N, args.members
+    dtype = B.NS3D_F32 if args.dtype == "f32" else B.NS3D_F64
+    esz = 8 if dtype == B.NS3D_F32 else 16
+    stream = torch.cuda.current_stream()
+    plan = B.Plan([N] * M, dtype, eps0=1.0, cfl=0.5)
+    P = plan.info(0)["P"]
+    u0 = [I.random_spectrum(N, seed=20240001 + rank * 1000 + m) for m in range(M)]
+    for m in range(M):
+        plan.set_initial(m, u0[m])
+
+    # warm-up (graph capture happens here)
+    plan.step(args.warmup)
+    plan.synchronize()
+
+    smi_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clocks = ClockSampler(smi_index)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.start()
+    time.sleep(0.25)
+    e0.record(stream)
+    plan.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    time.sleep(0.1)
+    ck = clocks.stop()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    status_ok = True
+    try:
+        plan.synchronize()
+    except B.Ns3dError:
+        status_ok = False
+    launches = plan.info(0)["launches_per_step"] * args.steps
+
+    # per-kernel durations: same kernels, eager, CUDA events on the plan's stream
+    kms, kn = plan.step_timed(max(3, min(20, args.steps // 10)))
+    kb = kernel_bytes(N, P, esz, M)
+    per_kind = {}
+    for i, k in enumerate(KINDS):
+        avg = kms[i] / max(kn[i], 1)
+        per_kind[k] = {"ms": avg, "GBps": kb[k] / (avg * 1e-3) / 1e9 if avg > 0 else None}
+    dom = max(range(6), key=lambda i: kms[i])
+    peak, peak_kind = measured_peaks()
+    dom_ms = kms[dom] / max(kn[dom], 1)
+    ach = kb[KINDS[dom]] / (dom_ms * 1e-3) / 1e9
+    step_bytes = 3 * sum(kb[k] for k in KINDS[:5]) + kb["spectral"] * 3
+    step_ms_eager = sum(kms) / max(kn[0] / 3, 1)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        npd = np.complex64 if dtype == B.NS3D_F32 else np.complex128
+        hin = [torch.from_numpy(np.ascontiguousarray(u.astype(npd))).pin_memory().numpy() for u in u0]
+        hout = [torch.empty(u.shape, dtype=plan.cdtype).pin_memory().numpy() for u in u0]
+        nb = sum(h.nbytes for h in hin)
+        ke = max(3, min(20, args.steps // 10))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for m in range(M):
+                plan.set_initial_host(m, hin[m])
+            plan.step(1)
+            for m in range(M):
+                plan.get_state_host(m, hout[m])
+        t1 = time.perf_counter()
+        et = max_over_ranks(t1 - t0)
+        e2e = {"value": world * M * N ** 3 * ke / et, "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+    value = world * M * N ** 3 * args.steps / (ms * 1e-3)
+    if rank != 0:
+        plan.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": f"{N}^3 random-spectrum sample{'s' if M > 1 else ''} per GPU "
+                               f"(k0 = 4, E = 0.5), CFL 0.5, hyper-viscosity s = 1.5, theta = 1/2",
+                   "N": N, "P": P, "members_per_gpu": M,
+                   "l2": "no flush: each step streams ~%.1f GB through HBM (> 126 MB L2)" % (step_bytes / 1e9),
+                   "parallelism": f"{world} GPU(s), one sample each (ensemble shards)"},
+        "samples_steps_per_s": world * M * args.steps / (ms * 1e-3),
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": KINDS[dom], "achieved": ach, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                     "bytes_per_launch": kb[KINDS[dom]], "traffic": None},
+        "step_roofline": {"bytes_per_step": step_bytes,
+                          "achieved_GBps": step_bytes / (ms / args.steps * 1e-3) / 1e9,
+                          "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},
+        "kernels": per_kind,
+        "eager_ms_per_step": step_ms_eager,
+        "clocks": ck,
+        "e2e": e2e,
+        "status_ok": status_ok,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ns3d.h - C ABI of the GB300 spectral hyper-viscosity solver for the 3D
+ * incompressible Navier-Stokes / Euler equations on the periodic torus.
+ *
+ * Method (Rohner & Mishra, "Efficient Computation of Large-Scale Statistical
+ * Solutions to Incompressible Fluid Flows", PASC'24):
+ *   - spatial discretisation: eq. shv_disc (section 2.2) with the Fourier
+ *     multiplier Q_N and the scalings m_N ~ N^theta, eps_N ~ N^(1-2s);
+ *   - Fourier-space evolution with the pressure eliminated by the Leray
+ *     projection (section 2.3), d/dt u_k = (I - k k^T/|k|^2) b_k,
+ *     b_k = -i k^T . F[u (x) u]_k, computed by Algorithm 2 (pad to >= 3N/2,
+ *     inverse FFT, product, forward FFT, remove the upper third, derivative);
+ *   - axis-by-axis padding fused with the transforms (Algorithm 3, section 3.2);
+ *   - SSP-RK3 time stepping (section 2.3, eq. RK3);
+ *   - Monte Carlo ensembles and their statistics (Algorithm 1, section 2.1;
+ *     writers, section 2.4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Fourier coefficients ("D1 layout"): for a member of resolution N (even),
+ *   complex array [3][N][N][N/2+1], index [component][kx][ky][kz], kz fastest,
+ *   wavenumber k = i for i < N/2 and i - N otherwise (x, y), kz = 0..N/2,
+ *   u_hat_k = N^-3 sum_x u(x) exp(-i kappa.x), kappa = (2 pi / L) k,
+ *   u(x) = sum over the full spectrum of u_hat_k exp(i kappa.x).
+ * Element type: interleaved complex of the plan's dtype (NS3D_F32: 2 floats,
+ *   NS3D_F64: 2 doubles).  Only the retained modes |k_i| <= N/2 - 1 are kept
+ *   (the projection P_N of eq. shv_disc): Nyquist planes are ignored on input
+ *   and returned as zero.
+ * Pointers: "on_device" arguments say whether a pointer is device memory of
+ *   the plan's GPU (non-zero) or host memory (zero).  The caller owns every
+ *   buffer it passes; device buffers must stay valid until the plan's stream
+ *   has passed the call.  The plan owns all workspaces it allocates.
+ * Streams: every call is ordered on the CUDA stream given at plan creation;
+ *   calls with host buffers synchronise that stream before returning.
+ * Errors: every call returns an ns3d_status and never aborts.  Conditions
+ *   found on the device (a non-finite velocity, lambda_max * dt above the
+ *   SSP-RK3 stability limit 2.5) are sticky per member and reported by the
+ *   next call that synchronises (ns3d_synchronize, ns3d_get_state,
+ *   ns3d_ensemble_stats).
+ */
+#ifndef NS3D_H
+#define NS3D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ns3d_plan_s* ns3d_plan;
+
+typedef enum {
+  NS3D_OK = 0,
+  NS3D_ERR_INVALID_ARG = 1,    /* bad size, index, pointer or parameter */
+  NS3D_ERR_OUT_OF_MEMORY = 2,  /* workspace above the limit, or cudaMalloc failed */
+  NS3D_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  NS3D_ERR_NONFINITE = 4,      /* a member's velocity became NaN/Inf */
+  NS3D_ERR_UNSTABLE_DT = 5,    /* lambda_max * dt > 2.5 for some member */
+  NS3D_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+  NS3D_ERR_NOT_SUPPORTED = 7   /* e.g. a padded size with a prime factor > 7 */
+} ns3d_status;
+
+typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
+
+/* Parameters of eq. shv_disc and of the time step.
+ *   lambda_k = nu |kappa|^2 + eps_N |kappa|^(2s) Q_k   (damping of mode k)
+ *   eps_N = eps0 * N^(1-2s),  m_N = mN_coef * N^theta
+ *   Q_k = 0 for |k| <= m_N, else 1 - (m_N/|k|)^((2s-1)/theta) (q_form 0) or 1 (q_form 1)
+ *   (|k| the integer wavenumber; the paper's "+eps_N" is read as damping).
+ *   n_pad: padded FFT size P (0: smallest 2^a 3^b 5^c 7^d >= 3N/2, section 3.1;
+ *          values below 3N/2 alias and are rejected).
+ *   nonlinear_form: 0 = divergence form -i k.F[u (x) u] (the paper's; the only
+ *          one the GPU path implements; 1 and 2 return NS3D_ERR_NOT_SUPPORTED).
+ *   dt_fixed > 0: fixed time step; otherwise dt = cfl * (L/N) / max_x sum_i |u_i|
+ *          evaluated on the padded grid of the stage-1 field, per member. */
+typedef struct {
+  double L;
+  double nu;
+  double s;
+  double theta;
+  double eps0;
+  double mN_coef;
+  int q_form;
+  int n_pad;
+  int nonlinear_form;
+  double cfl;
+  double dt_fixed;
+} ns3d_params;
+
+/* Fills *p with L = 2 pi, nu = 0, s = 1.5, theta = 0.5, eps0 = 1, mN_coef = 1,
+ * q_form = 0, n_pad = 0, nonlinear_form = 0, cfl = 0.5, dt_fixed = 0. */
+void ns3d_params_default(ns3d_params* p);
+
+/* Creates a plan for an ensemble of `batch` members (Algorithm 1), member i of
+ * resolution N_per_member[i] (even, >= 4).  Members of equal N form one level
+ * and advance together.  dtype selects the arithmetic of the whole path.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) of the current
+ * device.  workspace_limit_bytes: 0 = no limit; otherwise the plan fails with
+ * NS3D_ERR_OUT_OF_MEMORY before allocating if it would need more.
+ * Members start at u = 0, t = 0.  Errors: INVALID_ARG (sizes, params, null),
+ * NOT_SUPPORTED (padded size not 7-smooth or nonlinear_form != 0),
+ * OUT_OF_MEMORY, CUDA. */
+ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member, int batch, ns3d_dtype dtype,
+                             const ns3d_params* p, void* cuda_stream,
+                             size_t workspace_limit_bytes);
+
+/* Releases every device resource of the plan (synchronises its stream). */
+ns3d_status ns3d_plan_destroy(ns3d_plan plan);
+
+/* Describes the plan: padded size P of `member`'s level, bytes of device
+ * memory the plan holds, and number of kernels one ns3d_step launches. */
+ns3d_status ns3d_plan_info(ns3d_plan plan, int member, int* N, int* P, size_t* device_bytes,
+                           int* launches_per_step);
+
+/* Sets member `member`'s coefficients (D1 layout, plan dtype) and resets its
+ * time to 0 (initial data u(0) = P_N u0 of eq. shv_disc). */
+ns3d_status ns3d_set_initial(ns3d_plan plan, int member, const void* uhat, int uhat_on_device);
+
+/* Copies member `member`'s coefficients out (D1 layout, Nyquist planes zero)
+ * and, if t_out is not NULL, its time.  Synchronises; returns the member's
+ * sticky device status (NONFINITE / UNSTABLE_DT) if one was raised. */
+ns3d_status ns3d_get_state(ns3d_plan plan, int member, void* uhat_out, int out_on_device,
+                           double* t_out);
+
+/* Advances every member by `nsteps` SSP-RK3 steps (eq. RK3; three evaluations
+ * of Algorithm 2 each).  t_end > 0: a member's step is clipped so it stops at
+ * t_end exactly, and members already at t_end do not move.  Asynchronous: the
+ * work is a CUDA graph replayed on the plan's stream. */
+ns3d_status ns3d_step(ns3d_plan plan, int nsteps, double t_end);
+
+/* Waits for the plan's stream and returns the first sticky device status of
+ * any member (NS3D_OK if none). */
+ns3d_status ns3d_synchronize(ns3d_plan plan);
+
+/* Evaluates the time derivative d/dt u_hat = R(u_hat) of section 2.3
+ * (Algorithm 2) for one field of member `member`'s resolution, without
+ * touching the member's state.  uhat in and rhs_out in D1 layout. */
+ns3d_status ns3d_eval_rhs(ns3d_plan plan, int member, const void* uhat, void* rhs_out,
+                          int on_device);
+
+/* Discrete adjoint of one SSP-RK3 step (not in the paper; the exact transpose
+ * of eq. RK3 and of the linearised right-hand side of section 2.3 in the real
+ * inner product <a,b> = Re sum_k conj(a_k) b_k over the full spectrum).
+ * Given the forward state uhat_n at the start of the step and the adjoint
+ * lambda_np1 of the state after it, writes lambda_n = (d u_{n+1}/d u_n)^T
+ * lambda_np1.  The stages are recomputed from uhat_n.  The step uses the
+ * plan's dt_fixed (must be > 0; dt does not depend on u).  All arrays D1
+ * layout, plan dtype, device or host per on_device.  Member's state unchanged. */
+ns3d_status ns3d_adjoint_step(ns3d_plan plan, int member, const void* lambda_np1, void* lambda_n,
+                              const void* uhat_n, int on_device);
+
+/* Gradient of the band energy J = 1/2 sum_{k_lo <= |k| < k_hi} |u_hat_k(T)|^2
+ * (full spectrum) after nsteps fixed steps of dt_fixed, with respect to the
+ * member's current state u_hat(0), by the discrete adjoint.  States are kept
+ * every `checkpoint_every` steps (<= 0: every step) and recomputed inside
+ * each segment.  grad_uhat0 in D1 layout.  The member's state is unchanged. */
+ns3d_status ns3d_grad_band_energy(ns3d_plan plan, int member, double k_lo, double k_hi,
+                                  int nsteps, int checkpoint_every, void* grad_uhat0,
+                                  int on_device);
+
+/* Ensemble statistics of the members of resolution level_N at their current
+ * state (writers of section 2.4; Algorithm 1 step 3), accumulated in FP64 on
+ * the device.  Every array is host memory owned by the caller; any pointer may
+ * be NULL to skip that output.
+ *   mean          [3][N][N][N]  sample mean of u_i at the N^3 grid points x_j = j L/N
+ *   second        [6][N][N][N]  sample mean of u_i u_j (order 00 01 02 11 12 22)
+ *   var           [3][N][N][N]  sample variance of u_i (divisor M-1; 0 if M = 1)
+ *   spectrum      [N]           mean of E(K) = 1/2 sum_{round|k| = K} |u_hat_k|^2
+ *   spectrum_se   [N]           its Monte Carlo standard error sqrt(var/M)
+ *   s2, s2_se     [N/2]         mean and standard error of
+ *                               S2(r) = (1/3) sum_d <|u(x + r e_d) - u(x)|^2>, r = jL/N
+ *   energy, energy_se           mean and standard error of E = 1/2 <|u|^2>
+ *   members                     M, the number of members of the level */
+typedef struct {
+  double* mean;
+  double* second;
+  double* var;
+  double* spectrum;
+  double* spectrum_se;
+  double* s2;
+  double* s2_se;
+  double energy;
+  double energy_se;
+  int members;
+} ns3d_stats;
+
+ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);
+
+/* Diagnostic: advances every member by `nsteps` steps like ns3d_step, but
+ * launches the kernels one by one (no graph) with CUDA events recorded on the
+ * plan's stream around each of them, and adds the measured milliseconds of
+ * each kernel kind to kernel_ms[0..5] and the number of launches to
+ * launches[0..5] (kinds: 0 inverse x, 1 inverse y, 2 fused z pass, 3 forward
+ * y, 4 forward x, 5 spectral step).  Synchronises.  The paper times single
+ * kernel calls the same way to compare them with lower bounds (Table 2). */
+ns3d_status ns3d_step_timed(ns3d_plan plan, int nsteps, double t_end, double* kernel_ms,
+                            int* launches);
+
+/* Static text for a status code. */
+const char* ns3d_status_string(ns3d_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS3D_H */

@@ -211,3 +211,30 @@ def _energy_d1(uhat: np.ndarray) -> float:
     if N % 2 == 0:
         w[-1] = 1.0
     return 0.5 * float(np.sum(np.abs(uhat) ** 2 * w))
+
+
+def sparse_random(N: int, seed: int, nmodes: int = 40, kmax: int = 0, energy: float = 0.5) -> np.ndarray:
+    """A real divergence-free field with ``nmodes`` random retained modes
+    (|k_i| < kmax, default N/2), each i k x g / |k| for a Gaussian g, scaled
+    to the given energy.  Sparse spectra let the Galerkin product be summed
+    mode pair by mode pair at any N."""
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), 97])))
+    h = N // 2
+    kmax = kmax or h
+    uhat = np.zeros((3, N, N, h + 1), dtype=np.complex128)
+    for _ in range(nmodes):
+        k = rng.integers(-(kmax - 1), kmax, size=3)
+        k[2] = abs(k[2])
+        if not k.any():
+            continue
+        g = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        v = 1j * np.cross(k, g) / np.linalg.norm(k)
+        ix, iy = int(k[0]) % N, int(k[1]) % N
+        if k[2] == 0:   # keep the kz = 0 plane Hermitian
+            uhat[:, ix, iy, 0] += v
+            uhat[:, (-int(k[0])) % N, (-int(k[1])) % N, 0] += np.conj(v)
+        else:
+            uhat[:, ix, iy, int(k[2])] += v
+    uhat = truncate(uhat)
+    e = _energy_d1(uhat)
+    return uhat * np.sqrt(energy / e) if e > 0 else uhat

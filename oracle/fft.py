@@ -47,7 +47,13 @@ def dft_direct(x: np.ndarray, sign: int = -1) -> np.ndarray:
 
 
 def fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
-    """Unnormalised DFT along the last axis, X[k] = sum_j x[j] w_n^{jk}."""
+    """Unnormalised DFT along the last axis, X[k] = sum_j x[j] w_n^{jk}.
+
+    Decimation in time with n = p m: the p sub-sequences x[r::p] are
+    transformed together (one recursive call on an (..., p, m) array), then
+    for k = k1 + m k2
+        X[k1 + m k2] = sum_r w_p^{r k2} (w_n^{r k1} Y_r[k1]),
+    i.e. a twiddle multiply followed by a p-point DFT across r."""
     x = np.asarray(x, dtype=np.complex128)
     n = x.shape[-1]
     if n == 1:
@@ -56,12 +62,14 @@ def fft(x: np.ndarray, sign: int = -1) -> np.ndarray:
     if p == n:
         return dft_direct(x, sign)
     m = n // p
-    k = np.arange(n)
-    out = np.zeros(x.shape, dtype=np.complex128)
-    for r in range(p):
-        y = fft(x[..., r::p], sign)
-        out += _twiddle(r * k, n, sign) * y[..., k % m]
-    return out
+    sub = np.swapaxes(x.reshape(x.shape[:-1] + (m, p)), -1, -2)     # [..., r, j] = x[j p + r]
+    Y = fft(sub, sign)                                               # [..., r, k1]
+    r = np.arange(p)[:, None]
+    k1 = np.arange(m)[None, :]
+    T = Y * _twiddle(r * k1, n, sign)
+    Wp = _twiddle(np.outer(np.arange(p), np.arange(p)), p, sign)     # [k2, r]
+    X = np.matmul(Wp, T)                                             # [..., k2, k1]
+    return X.reshape(x.shape[:-1] + (n,))
 
 
 def fft_axis(x: np.ndarray, axis: int, sign: int = -1) -> np.ndarray:

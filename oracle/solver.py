@@ -328,3 +328,43 @@ def integrate(uhat: np.ndarray, prm: Params, nsteps: int, P: int | None = None,
 def rk3_amplification(z: complex) -> complex:
     """Stability polynomial of SSP-RK3 for u' = z u / dt: 1 + z + z^2/2 + z^3/6."""
     return 1.0 + z + z * z / 2.0 + z ** 3 / 6.0
+
+
+# ---------------------------------------------------------------- sparse fields
+
+def nonlinear_by_convolution(uhat: np.ndarray, prm: Params) -> np.ndarray:
+    """b_hat of the divergence form from the Galerkin definition of the
+    truncated product, B_hat_k = sum_{p + q = k} u_hat_p (x) u_hat_q over the
+    full spectrum, for k in K_N.  Cost grows with the square of the number of
+    nonzero modes: meant for sparse spectra at any N (no transform, no grid)."""
+    N = uhat.shape[-2]
+    h = N // 2
+    kx, ky, kz = wavenumbers(N)
+    shape = (N, N, N // 2 + 1)
+    m = np.any(uhat != 0, axis=0) & retained_mask(N)
+    K = np.stack([np.broadcast_to(kx, shape)[m], np.broadcast_to(ky, shape)[m],
+                  np.broadcast_to(kz, shape)[m]], axis=1)
+    V = uhat[:, m].T                                   # (nmodes, 3)
+    pos = K[:, 2] > 0                                  # mirror kz > 0 to -k
+    K = np.concatenate([K, -K[pos]])
+    V = np.concatenate([V, np.conj(V[pos])])
+    ksum = K[:, None, :] + K[None, :, :]               # (n, n, 3)
+    keep = (np.abs(ksum[..., 0]) < h) & (np.abs(ksum[..., 1]) < h) & (ksum[..., 2] >= 0) & (ksum[..., 2] < h)
+    ii, jj = np.nonzero(keep)
+    ks = ksum[ii, jj]
+    a = 2 * np.pi / prm.L
+    B = np.zeros((3, 3) + shape, dtype=np.complex128)
+    ix, iy, iz = ks[:, 0] % N, ks[:, 1] % N, ks[:, 2]
+    for j in range(3):
+        for l in range(3):
+            np.add.at(B[j, l], (ix, iy, iz), V[ii, j] * V[jj, l])
+    kap = kappa(N, prm.L)
+    b = np.stack([-1j * sum(kap[l] * B[j, l] for l in range(3)) for j in range(3)])
+    return b * retained_mask(N)
+
+
+def rhs_by_convolution(uhat: np.ndarray, prm: Params) -> np.ndarray:
+    """R(u_hat) with the nonlinear term from ``nonlinear_by_convolution``."""
+    N = uhat.shape[-2]
+    b = nonlinear_by_convolution(uhat, prm)
+    return (leray(b, prm.L) - dissipation(N, prm) * uhat) * retained_mask(N)

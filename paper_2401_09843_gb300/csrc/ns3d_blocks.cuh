@@ -1,0 +1,426 @@
+// Block bodies of the solver's kernels (one CUDA block each).
+//
+// Every function here takes the block index, the thread index/count, a
+// shared-memory pointer and a barrier functor, so the same code runs as a
+// CUDA block (kernels_*.cu) and, block by block with one emulated thread, on
+// the CPU (hostcheck.cpp) where the tests compare it with the oracle.
+//
+// Data layout in device memory (per ensemble level: B members of size N, padded
+// size P, h = N/2; all complex, interleaved re/im):
+//   state   U  [B][3][kx N][ky N][kz h]    retained modes; kz = N/2 is dropped,
+//                                         rows kx = h and ky = h stay zero
+//   A  (inverse x done)   [B][3][x P][ky N][kz h]
+//   Bq (inverse x,y done) [B][3][x P][kz h][y P]     y contiguous
+//   Cq (products, fwd z)  [B][6][x P][kz h][y P]
+//   Dq (fwd z,y)          [B][6][x P][ky N][kz h]
+//   Bh (fwd z,y,x)        [B][6][kx N][ky N][kz h]
+// The product components are ordered B00 B01 B02 B11 B12 B22.
+#pragma once
+
+#include "ns3d_fft.cuh"
+
+NS3D_HD int imin(int a, int b) { return a < b ? a : b; }
+NS3D_HD float xpow(float a, float b) { return powf(a, b); }
+NS3D_HD double xpow(double a, double b) { return pow(a, b); }
+
+// Per-member control word kept in device memory.
+struct Ns3dCtrl {
+  double t;                      // time reached
+  double dt;                     // time step of the step in progress (set at stage 1)
+  double t_end;                  // stop time (<= 0: none); a member at t_end stays put
+  unsigned long long umax_bits;  // max_x sum_i |u_i| of the stage-1 field (double bits)
+  int status;                    // sticky NS3D_FLAG_* bits
+  int nsteps;                    // completed steps
+};
+
+#define NS3D_FLAG_NONFINITE 1
+#define NS3D_FLAG_UNSTABLE 2
+
+NS3D_HD void atomic_max_u64(unsigned long long* p, unsigned long long v) {
+#if defined(__CUDA_ARCH__)
+  atomicMax(p, v);
+#else
+  if (*p < v) *p = v;
+#endif
+}
+
+NS3D_HD void atomic_or_i32(int* p, int v) {
+#if defined(__CUDA_ARCH__)
+  atomicOr(p, v);
+#else
+  *p |= v;
+#endif
+}
+
+NS3D_HD unsigned long long dbl_bits(double d) {
+#if defined(__CUDA_ARCH__)
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  union { double d; unsigned long long u; } c;
+  c.d = d;
+  return c.u;
+#endif
+}
+
+NS3D_HD double bits_dbl(unsigned long long u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  union { double d; unsigned long long u; } c;
+  c.u = u;
+  return c.d;
+#endif
+}
+
+// =====================================================================
+// Column pass: 1D transforms along one axis of a strided array
+// (Algorithm 3 steps 1-2 for the inverse with padding; the forward transform
+// with truncation is Algorithm 3 run in reverse, "remove the upper third").
+// =====================================================================
+template <typename T>
+struct ColArgs {
+  const cplx<T>* in;
+  cplx<T>* out;
+  const cplx<T>* tw;     // exp(-2 pi i e / n), e < n
+  FftPlanDev pl;
+  int h;                 // N/2
+  int nrow_in, nrow_out; // rows of the input / output arrays along the axis
+  int pad_in;            // input has N rows, spread over the n positions (zero pad)
+  int trunc_out;         // output keeps N rows of the n positions
+  int ncols;             // columns per (batch, outer) slice
+  int W, ldw;            // columns per block, padded shared row length
+  long long in_bs, in_os, in_cs, in_rs;    // batch / outer / column / row strides
+  long long out_bs, out_os, out_cs, out_rs;
+  T scale;
+};
+
+template <typename T>
+struct ColLoad {
+  const cplx<T>* in;
+  long long cs, rs;
+  int n, h, nrow, pad;
+  NS3D_HD cplx<T> operator()(int col, int p) const {
+    const int row = pad ? pad_row_of(p, n, h, nrow) : p;
+    if (row < 0) return czero<T>();
+    return in[col * cs + row * rs];
+  }
+};
+
+template <typename T>
+struct ColStore {
+  cplx<T>* out;
+  long long cs, rs;
+  int n, h, nrow, trunc;
+  T scale;
+  NS3D_HD void operator()(int col, int p, cplx<T> v) const {
+    const int row = trunc ? pad_row_of(p, n, h, nrow) : p;
+    if (row >= 0) out[col * cs + row * rs] = scale * v;
+  }
+};
+
+template <typename T, int SIGN, bool CF_FIRST, bool CF_LAST, class Sync>
+NS3D_HD void colfft_block(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
+                          cplx<T>* sm, const Sync& sync) {
+  const int c0 = bx * a.W;
+  const int ncol = imin(a.W, a.ncols - c0);
+  if (ncol <= 0) return;
+  const cplx<T>* in = a.in + bz * a.in_bs + by * a.in_os + c0 * a.in_cs;
+  cplx<T>* out = a.out + bz * a.out_bs + by * a.out_os + c0 * a.out_cs;
+  const int n = a.pl.n;
+  ColLoad<T> ld{in, a.in_cs, a.in_rs, n, a.h, a.nrow_in, a.pad_in};
+  ColStore<T> st{out, a.out_cs, a.out_rs, n, a.h, a.nrow_out, a.trunc_out, a.scale};
+  fft_tile<T, SIGN, CF_FIRST, CF_LAST>(a.pl, ncol, tid, nthr, a.tw, ld, st, sm, sm + n * a.ldw,
+                                       a.ldw, sync);
+  if (a.trunc_out) {
+    // the Nyquist row N/2 receives no position: keep it zero
+    for (int col = tid; col < ncol; col += nthr) out[col * a.out_cs + a.h * a.out_rs] = czero<T>();
+  }
+}
+
+// =====================================================================
+// Fused z pass (Algorithm 2 steps 2-4 along the last axis): complex-to-real
+// inverse of the three velocity components with the kz padding, the six
+// products B_jl = u_j u_l on the padded grid, the CFL maximum, and the
+// real-to-complex forward transform truncated to kz < N/2.  Two real lines
+// share one complex transform (z = a + i b; A_k = (Z_k + conj Z_{n-k})/2,
+// B_k = (Z_k - conj Z_{n-k})/(2i)).  Nothing physical is written to memory.
+// =====================================================================
+template <typename T>
+struct ZArgs {
+  const cplx<T>* in;   // Bq
+  cplx<T>* out;        // Cq
+  const cplx<T>* tw;   // length P
+  FftPlanDev pl;
+  int P, h, W, ldw;
+  long long in_bs, in_cs;    // member / component strides of Bq
+  long long out_bs, out_cs;  // member / component strides of Cq
+  long long xs;              // x stride (h * P) of both
+  Ns3dCtrl* ctrl;            // per member (null: no CFL reduction)
+};
+
+// u_a + i u_b packed spectrum from the stored half spectra (row q, column col)
+template <typename T>
+NS3D_HD cplx<T> pack2(const cplx<T>* ia, const cplx<T>* ib, int P, int h, int p, int ca, int cb,
+                      int ncol) {
+  cplx<T> a = czero<T>(), b = czero<T>();
+  if (p < h) {
+    if (ca < ncol) a = ia[p * P + ca];
+    if (cb < ncol) b = ib[p * P + cb];
+    if (p == 0) {
+      a.y = T(0);   // a real line has a real mean: keep the Hermitian part
+      b.y = T(0);
+    }
+  } else if (p > P - h) {
+    const int q = P - p;
+    if (ca < ncol) a = cconj(ia[q * P + ca]);
+    if (cb < ncol) b = cconj(ib[q * P + cb]);
+  } else {
+    return czero<T>();
+  }
+  return cmake(a.x - b.y, a.y + b.x);
+}
+
+template <typename T>
+struct ZLoadInv {
+  const cplx<T>* ia;
+  const cplx<T>* ib;
+  int P, h, ncol, pair_off;  // pair_off = 0: (u0,u1) same column; else u2 columns (m, m+off)
+  NS3D_HD cplx<T> operator()(int col, int p) const {
+    if (pair_off == 0) return pack2(ia, ib, P, h, p, col, col, ncol);
+    return pack2(ia, ib, P, h, p, col, col + pair_off, ncol);
+  }
+};
+
+template <typename T>
+struct ZPhys {  // physical velocity at (position p, column col) from the inverse results
+  const cplx<T>* U01;
+  const cplx<T>* U2;
+  int ldw, half;
+  NS3D_HD void get(int col, int p, T& u0, T& u1, T& u2) const {
+    const cplx<T> z = U01[p * ldw + col];
+    u0 = z.x;
+    u1 = z.y;
+    u2 = (col < half) ? U2[p * ldw + col].x : U2[p * ldw + col - half].y;
+  }
+};
+
+template <typename T>
+struct ZLoadProd {
+  ZPhys<T> ph;
+  int pair;
+  NS3D_HD cplx<T> operator()(int col, int p) const {
+    T u0, u1, u2;
+    ph.get(col, p, u0, u1, u2);
+    if (pair == 0) return cmake(u0 * u0, u0 * u1);
+    if (pair == 1) return cmake(u0 * u2, u1 * u1);
+    return cmake(u1 * u2, u2 * u2);
+  }
+};
+
+template <typename T, class Sync>
+NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
+                          cplx<T>* sm, double* red, const Sync& sync) {
+  const int P = a.P, h = a.h, W = a.W, ldw = a.ldw;
+  const int y0 = bx * W;
+  const int ncol = imin(W, P - y0);
+  const int half = W / 2;
+  cplx<T>* U01 = sm;
+  cplx<T>* U2 = sm + P * ldw;
+  cplx<T>* A = sm + 2 * P * ldw;
+  cplx<T>* B = sm + 3 * P * ldw;
+  const cplx<T>* in = a.in + bz * a.in_bs + by * a.xs + y0;
+  SmemIO<T> u01{U01, ldw}, u2s{U2, ldw};
+
+  // inverse: (u0 + i u1) per column, and u2 of columns (m, m + W/2) per pair
+  ZLoadInv<T> l01{in, in + a.in_cs, P, h, ncol, 0};
+  fft_tile<T, +1, true, true>(a.pl, ncol, tid, nthr, a.tw, l01, u01, A, B, ldw, sync);
+  sync();
+  ZLoadInv<T> l22{in + 2 * a.in_cs, in + 2 * a.in_cs, P, h, ncol, half};
+  fft_tile<T, +1, true, true>(a.pl, half, tid, nthr, a.tw, l22, u2s, A, B, ldw, sync);
+  sync();
+
+  ZPhys<T> ph{U01, U2, ldw, half};
+  if (a.ctrl) {
+    double m = 0.0;
+    int bad = 0;
+    for (int w = tid; w < P * ncol; w += nthr) {
+      const int col = w % ncol, p = w / ncol;
+      T u0, u1, u2;
+      ph.get(col, p, u0, u1, u2);
+      const double s = fabs((double)u0) + fabs((double)u1) + fabs((double)u2);
+      if (!(s <= 1.0e300)) bad = 1;
+      else if (s > m) m = s;
+    }
+    red[tid] = bad ? -1.0 : m;
+    sync();
+    if (tid == 0) {
+      double mm = 0.0;
+      int anybad = 0;
+      for (int i = 0; i < nthr; ++i) {
+        if (red[i] < 0) anybad = 1;
+        else if (red[i] > mm) mm = red[i];
+      }
+      atomic_max_u64(&a.ctrl[bz].umax_bits, dbl_bits(mm));
+      if (anybad) atomic_or_i32(&a.ctrl[bz].status, NS3D_FLAG_NONFINITE);
+    }
+  }
+
+  // forward: three packed pairs of products, each truncated to kz < h
+  cplx<T>* out = a.out + bz * a.out_bs + by * a.xs + y0;
+  for (int pair = 0; pair < 3; ++pair) {
+    ZLoadProd<T> lp{ph, pair};
+    cplx<T>* E = fft_free_buffer(a.pl.npass, A, B);
+    SmemIO<T> e{E, ldw};
+    fft_tile<T, -1, true, true>(a.pl, ncol, tid, nthr, a.tw, lp, e, A, B, ldw, sync);
+    sync();
+    cplx<T>* oa = out + (2 * pair) * a.out_cs;
+    cplx<T>* ob = out + (2 * pair + 1) * a.out_cs;
+    for (int w = tid; w < h * ncol; w += nthr) {
+      const int col = w % ncol, k = w / ncol;
+      const cplx<T> zk = E[k * ldw + col];
+      const cplx<T> zm = cconj(E[((P - k) % P) * ldw + col]);
+      const cplx<T> s = zk + zm;
+      const cplx<T> d = zk - zm;
+      oa[k * P + col] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+      ob[k * P + col] = cmake(T(0.5) * d.y, T(-0.5) * d.x);   // d / (2i)
+    }
+    sync();
+  }
+}
+
+// =====================================================================
+// Spectral step (section 2.3 and eq. RK3): b = -i kappa . B_hat / P^3,
+// Leray projection, dissipation lambda_k u_k, and the SSP-RK3 stage combine.
+// =====================================================================
+struct SpecParams {
+  double kscale;      // 2 pi / L
+  double nu, epsN, s, mN2, qexp;
+  int kthr;           // |k|^2 <= kthr: no hyper-viscosity
+  int q_form;
+  double inv_P3;
+  double cfl, dx, dt_fixed, lam_max;
+};
+
+template <typename T>
+struct SpecArgs {
+  const cplx<T>* bh;   // Bh
+  const cplx<T>* u0;   // U at t_n
+  const cplx<T>* us;   // stage state (stages 2, 3)
+  cplx<T>* out;        // next stage / next state / R (stage 0)
+  int N, h, nmem;
+  int stage;           // 0: out = R; 1, 2, 3: RK3 stages
+  long long m6, m3;    // member strides of Bh and of U
+  SpecParams sp;
+  Ns3dCtrl* ctrl;
+};
+
+NS3D_HD double member_dt(const Ns3dCtrl& c, const SpecParams& sp) {
+  double dt;
+  const double umax = bits_dbl(c.umax_bits);
+  if (sp.dt_fixed > 0) dt = sp.dt_fixed;
+  else if (umax > 0) dt = sp.cfl * sp.dx / umax;
+  else dt = (c.t_end > 0) ? c.t_end - c.t : 0.0;
+  if (c.t_end > 0) {
+    const double rem = c.t_end - c.t;
+    if (dt > rem) dt = rem;
+    if (dt < 0) dt = 0;
+  }
+  return dt;
+}
+
+template <typename T>
+NS3D_HD T lambda_k(int k2, const SpecParams& sp) {
+  const T kap2 = T(sp.kscale * sp.kscale) * T(k2);
+  T lam = T(sp.nu) * kap2;
+  if (k2 > sp.kthr) {
+    T q = T(1);
+    if (sp.q_form == 0) q = T(1) - xpow((T)(sp.mN2 / (double)k2), (T)sp.qexp);
+    lam += T(sp.epsN) * xpow(kap2, (T)sp.s) * q;
+  }
+  return lam;
+}
+
+// One thread per (member, kx, ky, kz); `i` is the flat index.
+template <typename T>
+NS3D_HD void spectral_point(const SpecArgs<T>& a, long long i) {
+  const int h = a.h, N = a.N;
+  const int kz = (int)(i % h);
+  const int ky = (int)((i / h) % N);
+  const int kx = (int)((i / ((long long)h * N)) % N);
+  const int m = (int)(i / ((long long)h * N * N));
+  const long long off = (long long)(kx * N + ky) * h + kz;
+  const long long plane = (long long)N * N * h;
+  const cplx<T>* u0 = a.u0 + m * a.m3 + off;
+  cplx<T>* out = a.out + m * a.m3 + off;
+
+  double dt = 0.0;
+  if (a.stage >= 1) {
+    Ns3dCtrl& c = a.ctrl[m];
+    if (a.stage == 1) {
+      dt = member_dt(c, a.sp);
+      if (off == 0) {
+        c.dt = dt;
+        if (dt * a.sp.lam_max > 2.5) c.status |= NS3D_FLAG_UNSTABLE;
+      }
+    } else {
+      dt = c.dt;
+    }
+    if (dt <= 0.0) {   // member finished: stages leave it unchanged
+      if (out != u0)
+        for (int j = 0; j < 3; ++j) out[j * plane] = u0[j * plane];
+      if (a.stage == 3 && off == 0) c.umax_bits = 0ull;
+      return;
+    }
+  }
+
+  cplx<T> R[3];
+  const int sx = kx < h ? kx : kx - N;
+  const int sy = ky < h ? ky : ky - N;
+  const int k2 = sx * sx + sy * sy + kz * kz;
+  if (kx == h || ky == h || k2 == 0) {
+    R[0] = R[1] = R[2] = czero<T>();
+  } else {
+    const cplx<T>* bh = a.bh + m * a.m6 + off;
+    const T ks = T(a.sp.kscale);
+    const T kx_ = ks * T(sx), ky_ = ks * T(sy), kz_ = ks * T(kz);
+    const T sc = T(a.sp.inv_P3);
+    cplx<T> b6[6];
+    for (int c = 0; c < 6; ++c) b6[c] = sc * bh[c * plane];
+    // kappa . B_j  (B symmetric: 00 01 02 11 12 22)
+    const cplx<T> t0 = kx_ * b6[0] + ky_ * b6[1] + kz_ * b6[2];
+    const cplx<T> t1 = kx_ * b6[1] + ky_ * b6[3] + kz_ * b6[4];
+    const cplx<T> t2 = kx_ * b6[2] + ky_ * b6[4] + kz_ * b6[5];
+    // b = -i t
+    const cplx<T> bb[3] = {cmake(t0.y, -t0.x), cmake(t1.y, -t1.x), cmake(t2.y, -t2.x)};
+    const T kap2 = kx_ * kx_ + ky_ * ky_ + kz_ * kz_;
+    const cplx<T> kb = (T(1) / kap2) * (kx_ * bb[0] + ky_ * bb[1] + kz_ * bb[2]);
+    const T lam = lambda_k<T>(k2, a.sp);
+    // the dissipation acts on the field R is evaluated at: u_n at stages 0
+    // and 1, the stage state at stages 2 and 3
+    const cplx<T>* ue = (a.stage >= 2) ? a.us + m * a.m3 + off : u0;
+    R[0] = bb[0] - kx_ * kb - lam * ue[0];
+    R[1] = bb[1] - ky_ * kb - lam * ue[plane];
+    R[2] = bb[2] - kz_ * kb - lam * ue[2 * plane];
+  }
+
+  const T tdt = T(dt);
+  for (int j = 0; j < 3; ++j) {
+    const cplx<T> uj = u0[j * plane];
+    cplx<T> v;
+    if (a.stage == 0) v = R[j];
+    else if (a.stage == 1) v = uj + tdt * R[j];
+    else {
+      const cplx<T> w = a.us[m * a.m3 + off + j * plane] + tdt * R[j];
+      if (a.stage == 2) v = T(0.75) * uj + T(0.25) * w;
+      else v = T(1.0 / 3.0) * uj + T(2.0 / 3.0) * w;
+    }
+    if (kx == h || ky == h) v = czero<T>();
+    out[j * plane] = v;
+  }
+  if (a.stage == 3 && off == 0) {
+    Ns3dCtrl& c = a.ctrl[m];
+    c.t += dt;
+    c.nsteps += 1;
+    c.umax_bits = 0ull;
+  }
+}

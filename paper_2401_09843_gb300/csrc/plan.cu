@@ -1,0 +1,526 @@
+// C ABI of the solver (include/ns3d.h): plans, workspaces, the captured
+// step graph, state transfer and the right-hand-side evaluation.
+//
+// A plan groups its members by resolution into levels.  Each level owns
+//   U0   state u_n              [B][3][N][N][N/2]
+//   US   stage state u1 / u2    [B][3][N][N][N/2]
+//   W1   A  / Cq / Bh           (aliased workspaces, Workspaces of section 3.4:
+//   W2   Bq / Dq                 each is dead before the next pass reuses it)
+// and one RK3 stage is the pass sequence
+//   inverse x (pad) -> inverse y (pad) -> z: c2r, products, r2c (truncate)
+//   -> forward y (truncate) -> forward x (truncate) -> spectral step + combine,
+// i.e. Algorithm 2 with the padding fused into the transforms (Algorithm 3).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "ns3d.h"
+#include "ns3d_launch.h"
+
+using namespace ns3d;
+
+namespace {
+
+struct Level {
+  int N = 0, P = 0, B = 0;
+  Geom g;
+  SpecParams sp{};
+  std::vector<int> members;
+  void* U0 = nullptr;
+  void* US = nullptr;
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  void* twP = nullptr;
+  Ns3dCtrl* ctrl = nullptr;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct ns3d_plan_s {
+  int device = 0;
+  ns3d_dtype dtype = NS3D_F32;
+  int esz = 8;
+  ns3d_params prm{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<Level> levels;
+  std::vector<std::pair<int, int>> loc;  // member -> (level, index in level)
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  void* staging = nullptr;               // device buffer of one member in D1 layout
+  size_t staging_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double t_end = 0.0;
+  int launches_per_step = 0;
+};
+
+#define NS3D_CK(x)                            \
+  do {                                        \
+    if ((x) != cudaSuccess) return NS3D_ERR_CUDA; \
+  } while (0)
+
+extern "C" void ns3d_params_default(ns3d_params* p) {
+  if (!p) return;
+  p->L = 6.283185307179586476925286766559;
+  p->nu = 0.0;
+  p->s = 1.5;
+  p->theta = 0.5;
+  p->eps0 = 1.0;
+  p->mN_coef = 1.0;
+  p->q_form = 0;
+  p->n_pad = 0;
+  p->nonlinear_form = 0;
+  p->cfl = 0.5;
+  p->dt_fixed = 0.0;
+}
+
+extern "C" const char* ns3d_status_string(ns3d_status s) {
+  switch (s) {
+    case NS3D_OK: return "ok";
+    case NS3D_ERR_INVALID_ARG: return "invalid argument";
+    case NS3D_ERR_OUT_OF_MEMORY: return "out of memory";
+    case NS3D_ERR_CUDA: return "CUDA error";
+    case NS3D_ERR_NONFINITE: return "non-finite velocity";
+    case NS3D_ERR_UNSTABLE_DT: return "time step above the RK3 stability limit";
+    case NS3D_ERR_TIMEOUT: return "device wait timed out";
+    case NS3D_ERR_NOT_SUPPORTED: return "not supported";
+  }
+  return "unknown status";
+}
+
+namespace {
+
+ns3d_status dev_alloc(ns3d_plan p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) return NS3D_OK;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return NS3D_ERR_OUT_OF_MEMORY;
+  }
+  p->allocs.push_back(*ptr);
+  p->bytes += bytes;
+  return NS3D_OK;
+}
+
+void free_all(ns3d_plan p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  for (void* a : p->allocs) cudaFree(a);
+  p->allocs.clear();
+  if (p->cap) cudaStreamDestroy(p->cap);
+  p->cap = nullptr;
+}
+
+template <typename T>
+ns3d_status upload_twiddles(Level& L, cudaStream_t s) {
+  std::vector<cplx<T>> tw = make_twiddles<T>(L.P);
+  NS3D_CK(cudaMemcpyAsync(L.twP, tw.data(), tw.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, s));
+  NS3D_CK(cudaStreamSynchronize(s));
+  return NS3D_OK;
+}
+
+// One evaluation of Algorithm 2 plus the spectral step for members
+// [m0, m0 + nm) of a level.  `in` is the field R is evaluated at; stage 0
+// writes R to `out`, stages 1-3 the SSP-RK3 combinations.
+// Optional per-kernel timing: events recorded before each kernel kind.
+struct KernelTimer {
+  cudaEvent_t ev[7];
+  int kinds = 0;
+};
+
+#define NS3D_MARK(i) \
+  if (tm) NS3D_CK(cudaEventRecord(tm->ev[i], s))
+
+template <typename T>
+ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in, cplx<T>* out,
+                          bool want_umax, cudaStream_t s, KernelTimer* tm = nullptr) {
+  const Geom& g = L.g;
+  cplx<T>* W1 = static_cast<cplx<T>*>(L.W1);
+  cplx<T>* W2 = static_cast<cplx<T>*>(L.W2);
+  const cplx<T>* tw = static_cast<const cplx<T>*>(L.twP);
+  cplx<T>* U0 = static_cast<cplx<T>*>(L.U0) + m0 * g.nU;
+  cplx<T>* US = static_cast<cplx<T>*>(L.US) + m0 * g.nU;
+  NS3D_MARK(0);
+  NS3D_CK(launch_col<T>(args_inv_x<T>(g, in, W1, tw), COL_INV_CC, launch_inv_x(g, nm), s));
+  NS3D_MARK(1);
+  NS3D_CK(launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CT, launch_inv_y(g, nm), s));
+  NS3D_MARK(2);
+  NS3D_CK(launch_zfused<T>(args_z<T>(g, W2, W1, tw, want_umax ? L.ctrl + m0 : nullptr),
+                           launch_z(g, nm), s));
+  NS3D_MARK(3);
+  NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_TC, launch_fwd_y(g, nm), s));
+  NS3D_MARK(4);
+  NS3D_CK(launch_col<T>(args_fwd_x<T>(g, W2, W1, tw), COL_FWD_CC, launch_fwd_x(g, nm), s));
+  NS3D_MARK(5);
+  SpecArgs<T> a{};
+  a.bh = W1;
+  a.u0 = (stage == 0) ? in : U0;
+  a.us = US;
+  a.out = out;
+  a.N = g.N;
+  a.h = g.h;
+  a.nmem = nm;
+  a.stage = stage;
+  a.m6 = g.nBh;
+  a.m3 = g.nU;
+  a.sp = L.sp;
+  a.ctrl = L.ctrl + m0;
+  NS3D_CK(launch_spectral<T>(a, (long long)nm * g.N * g.N * g.h, s));
+  NS3D_MARK(6);
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status enqueue_step(ns3d_plan p, cudaStream_t s) {
+  for (Level& L : p->levels) {
+    cplx<T>* U0 = static_cast<cplx<T>*>(L.U0);
+    cplx<T>* US = static_cast<cplx<T>*>(L.US);
+    ns3d_status st;
+    if ((st = enqueue_stage<T>(L, 1, 0, L.B, U0, US, p->prm.dt_fixed <= 0, s)) != NS3D_OK) return st;
+    if ((st = enqueue_stage<T>(L, 2, 0, L.B, US, US, false, s)) != NS3D_OK) return st;
+    if ((st = enqueue_stage<T>(L, 3, 0, L.B, US, U0, false, s)) != NS3D_OK) return st;
+  }
+  return NS3D_OK;
+}
+
+ns3d_status build_graph(ns3d_plan p) {
+  if (p->exec) return NS3D_OK;
+  NS3D_CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+  ns3d_status st = p->dtype == NS3D_F32 ? enqueue_step<float>(p, p->cap) : enqueue_step<double>(p, p->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+  if (st != NS3D_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return NS3D_ERR_CUDA;
+  p->graph = g;
+  if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+    p->exec = nullptr;
+    return NS3D_ERR_CUDA;
+  }
+  return NS3D_OK;
+}
+
+ns3d_status member_lookup(ns3d_plan p, int member, Level** L, int* idx) {
+  if (!p || member < 0 || member >= (int)p->loc.size()) return NS3D_ERR_INVALID_ARG;
+  *L = &p->levels[p->loc[member].first];
+  *idx = p->loc[member].second;
+  return NS3D_OK;
+}
+
+size_t d1_bytes(int N, int esz) { return (size_t)3 * N * N * (N / 2 + 1) * esz; }
+
+// D1 (device or host) -> compact member slot
+template <typename T>
+ns3d_status put_d1(ns3d_plan p, Level& L, const void* src, int on_device, cplx<T>* dst) {
+  const size_t nb = d1_bytes(L.N, p->esz);
+  const void* dsrc = src;
+  if (!on_device) {
+    NS3D_CK(cudaMemcpyAsync(p->staging, src, nb, cudaMemcpyHostToDevice, p->stream));
+    dsrc = p->staging;
+  }
+  NS3D_CK(launch_d1_to_compact<T>(static_cast<const cplx<T>*>(dsrc), dst, L.N, p->stream));
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status get_d1(ns3d_plan p, Level& L, const cplx<T>* src, void* dst, int on_device) {
+  const size_t nb = d1_bytes(L.N, p->esz);
+  void* ddst = on_device ? dst : p->staging;
+  NS3D_CK(launch_compact_to_d1<T>(src, static_cast<cplx<T>*>(ddst), L.N, p->stream));
+  if (!on_device) NS3D_CK(cudaMemcpyAsync(dst, p->staging, nb, cudaMemcpyDeviceToHost, p->stream));
+  return NS3D_OK;
+}
+
+ns3d_status status_of_flags(int flags) {
+  if (flags & NS3D_FLAG_NONFINITE) return NS3D_ERR_NONFINITE;
+  if (flags & NS3D_FLAG_UNSTABLE) return NS3D_ERR_UNSTABLE_DT;
+  return NS3D_OK;
+}
+
+}  // namespace
+
+extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member, int batch,
+                                        ns3d_dtype dtype, const ns3d_params* prm,
+                                        void* cuda_stream, size_t workspace_limit_bytes) {
+  if (!out) return NS3D_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!N_per_member || batch <= 0 || (dtype != NS3D_F32 && dtype != NS3D_F64))
+    return NS3D_ERR_INVALID_ARG;
+  ns3d_params P;
+  if (prm) P = *prm;
+  else ns3d_params_default(&P);
+  if (!(P.L > 0) || !(P.nu >= 0) || !(P.s >= 0.5) || !(P.theta > 0) || !(P.eps0 >= 0) ||
+      !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < 0 ||
+      !(P.dt_fixed >= 0) || (P.dt_fixed == 0 && !(P.cfl > 0)))
+    return NS3D_ERR_INVALID_ARG;
+  if (P.nonlinear_form != 0) return NS3D_ERR_NOT_SUPPORTED;
+  std::map<int, std::vector<int>> byN;
+  for (int i = 0; i < batch; ++i) {
+    const int N = N_per_member[i];
+    if (N < 4 || N % 2 || N > 4096) return NS3D_ERR_INVALID_ARG;
+    byN[N].push_back(i);
+  }
+  ns3d_plan p = new (std::nothrow) ns3d_plan_s();
+  if (!p) return NS3D_ERR_OUT_OF_MEMORY;
+  p->dtype = dtype;
+  p->esz = dtype == NS3D_F32 ? 8 : 16;
+  p->prm = P;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  p->loc.resize(batch);
+  size_t need = 0, stag = 0;
+  for (auto& kv : byN) {
+    Level L;
+    L.N = kv.first;
+    L.B = (int)kv.second.size();
+    L.members = kv.second;
+    if (P.n_pad) {
+      if (2 * P.n_pad < 3 * L.N) { delete p; return NS3D_ERR_INVALID_ARG; }
+      L.P = P.n_pad;
+    } else {
+      L.P = default_padded_size(L.N);
+    }
+    if (!make_geom(L.N, L.P, p->esz, &L.g)) { delete p; return NS3D_ERR_NOT_SUPPORTED; }
+    L.sp = make_spec_params(L.N, L.P, P.L, P.nu, P.s, P.theta, P.eps0, P.mN_coef, P.q_form, P.cfl,
+                            P.dt_fixed);
+    const Geom& g = L.g;
+    need += (size_t)L.B * (2 * g.nU + g.nW1 + g.nW2) * p->esz + (size_t)L.P * p->esz +
+            (size_t)L.B * sizeof(Ns3dCtrl);
+    stag = std::max(stag, d1_bytes(L.N, p->esz));
+    for (int j = 0; j < L.B; ++j) p->loc[kv.second[j]] = {(int)p->levels.size(), j};
+    p->levels.push_back(L);
+  }
+  need += stag;
+  if (workspace_limit_bytes && need > workspace_limit_bytes) {
+    delete p;
+    return NS3D_ERR_OUT_OF_MEMORY;
+  }
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return NS3D_ERR_CUDA;
+  }
+  ns3d_status st = NS3D_OK;
+  if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) st = NS3D_ERR_CUDA;
+  if (st == NS3D_OK) {
+    cudaError_t e = dtype == NS3D_F32 ? kernels_init<float>() : kernels_init<double>();
+    if (e != cudaSuccess) st = NS3D_ERR_CUDA;
+  }
+  for (Level& L : p->levels) {
+    if (st != NS3D_OK) break;
+    const Geom& g = L.g;
+    if ((st = dev_alloc(p, &L.U0, (size_t)L.B * g.nU * p->esz)) != NS3D_OK) break;
+    if ((st = dev_alloc(p, &L.US, (size_t)L.B * g.nU * p->esz)) != NS3D_OK) break;
+    if ((st = dev_alloc(p, &L.W1, (size_t)L.B * g.nW1 * p->esz)) != NS3D_OK) break;
+    if ((st = dev_alloc(p, &L.W2, (size_t)L.B * g.nW2 * p->esz)) != NS3D_OK) break;
+    if ((st = dev_alloc(p, &L.twP, (size_t)L.P * p->esz)) != NS3D_OK) break;
+    void* c = nullptr;
+    if ((st = dev_alloc(p, &c, (size_t)L.B * sizeof(Ns3dCtrl))) != NS3D_OK) break;
+    L.ctrl = static_cast<Ns3dCtrl*>(c);
+    st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
+    if (st != NS3D_OK) break;
+    if (cudaMemsetAsync(L.U0, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
+        cudaMemsetAsync(L.US, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
+        launch_ctrl_reset(L.ctrl, L.B, p->stream) != cudaSuccess)
+      st = NS3D_ERR_CUDA;
+  }
+  if (st == NS3D_OK) st = dev_alloc(p, &p->staging, stag);
+  if (st == NS3D_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = NS3D_ERR_CUDA;
+  if (st != NS3D_OK) {
+    free_all(p);
+    delete p;
+    return st;
+  }
+  p->staging_bytes = stag;
+  p->launches_per_step = 18 * (int)p->levels.size();
+  *out = p;
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_plan_destroy(ns3d_plan p) {
+  if (!p) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  cudaStreamSynchronize(p->stream);
+  free_all(p);
+  delete p;
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_plan_info(ns3d_plan p, int member, int* N, int* P, size_t* bytes,
+                                      int* launches) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (N) *N = L->N;
+  if (P) *P = L->P;
+  if (bytes) *bytes = p->bytes;
+  if (launches) *launches = p->launches_per_step;
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_set_initial(ns3d_plan p, int member, const void* uhat, int on_device) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (!uhat) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  if (p->dtype == NS3D_F32)
+    st = put_d1<float>(p, *L, uhat, on_device, static_cast<cplx<float>*>(L->U0) + idx * L->g.nU);
+  else
+    st = put_d1<double>(p, *L, uhat, on_device, static_cast<cplx<double>*>(L->U0) + idx * L->g.nU);
+  if (st != NS3D_OK) return st;
+  NS3D_CK(launch_ctrl_reset(L->ctrl + idx, 1, p->stream));
+  NS3D_CK(launch_ctrl_set_tend(L->ctrl + idx, 1, p->t_end, p->stream));
+  if (!on_device) NS3D_CK(cudaStreamSynchronize(p->stream));
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_get_state(ns3d_plan p, int member, void* out, int on_device,
+                                      double* t_out) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (!out) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  if (p->dtype == NS3D_F32)
+    st = get_d1<float>(p, *L, static_cast<const cplx<float>*>(L->U0) + idx * L->g.nU, out, on_device);
+  else
+    st = get_d1<double>(p, *L, static_cast<const cplx<double>*>(L->U0) + idx * L->g.nU, out, on_device);
+  if (st != NS3D_OK) return st;
+  Ns3dCtrl c;
+  NS3D_CK(cudaMemcpyAsync(&c, L->ctrl + idx, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  NS3D_CK(cudaStreamSynchronize(p->stream));
+  if (t_out) *t_out = c.t;
+  return status_of_flags(c.status);
+}
+
+extern "C" ns3d_status ns3d_step(ns3d_plan p, int nsteps, double t_end) {
+  if (!p || nsteps < 0) return NS3D_ERR_INVALID_ARG;
+  if (nsteps == 0) return NS3D_OK;
+  DeviceGuard dg(p->device);
+  if (t_end != p->t_end) {
+    for (Level& L : p->levels) NS3D_CK(launch_ctrl_set_tend(L.ctrl, L.B, t_end, p->stream));
+    p->t_end = t_end;
+  }
+  ns3d_status st = build_graph(p);
+  if (st != NS3D_OK) return st;
+  for (int i = 0; i < nsteps; ++i) NS3D_CK(cudaGraphLaunch(p->exec, p->stream));
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_synchronize(ns3d_plan p) {
+  if (!p) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  NS3D_CK(cudaStreamSynchronize(p->stream));
+  int flags = 0;
+  for (Level& L : p->levels) {
+    std::vector<Ns3dCtrl> c(L.B);
+    NS3D_CK(cudaMemcpy(c.data(), L.ctrl, L.B * sizeof(Ns3dCtrl), cudaMemcpyDeviceToHost));
+    for (const Ns3dCtrl& x : c) flags |= x.status;
+  }
+  return status_of_flags(flags);
+}
+
+extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, void* rhs,
+                                     int on_device) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (!uhat || !rhs) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  if (p->dtype == NS3D_F32) {
+    cplx<float>* slot = static_cast<cplx<float>*>(L->US) + idx * L->g.nU;
+    if ((st = put_d1<float>(p, *L, uhat, on_device, slot)) != NS3D_OK) return st;
+    if ((st = enqueue_stage<float>(*L, 0, idx, 1, slot, slot, false, p->stream)) != NS3D_OK) return st;
+    if ((st = get_d1<float>(p, *L, slot, rhs, on_device)) != NS3D_OK) return st;
+  } else {
+    cplx<double>* slot = static_cast<cplx<double>*>(L->US) + idx * L->g.nU;
+    if ((st = put_d1<double>(p, *L, uhat, on_device, slot)) != NS3D_OK) return st;
+    if ((st = enqueue_stage<double>(*L, 0, idx, 1, slot, slot, false, p->stream)) != NS3D_OK) return st;
+    if ((st = get_d1<double>(p, *L, slot, rhs, on_device)) != NS3D_OK) return st;
+  }
+  if (!on_device) NS3D_CK(cudaStreamSynchronize(p->stream));
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_adjoint_step(ns3d_plan p, int member, const void* lambda_np1,
+                                         void* lambda_n, const void* uhat_n, int on_device) {
+  (void)p; (void)member; (void)lambda_np1; (void)lambda_n; (void)uhat_n; (void)on_device;
+  return NS3D_ERR_NOT_SUPPORTED;
+}
+
+extern "C" ns3d_status ns3d_grad_band_energy(ns3d_plan p, int member, double k_lo, double k_hi,
+                                             int nsteps, int checkpoint_every, void* grad,
+                                             int on_device) {
+  (void)p; (void)member; (void)k_lo; (void)k_hi; (void)nsteps; (void)checkpoint_every;
+  (void)grad; (void)on_device;
+  return NS3D_ERR_NOT_SUPPORTED;
+}
+
+extern "C" ns3d_status ns3d_ensemble_stats(ns3d_plan p, int level_N, ns3d_stats* out) {
+  (void)p; (void)level_N; (void)out;
+  return NS3D_ERR_NOT_SUPPORTED;
+}
+
+extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, double* kernel_ms,
+                                       int* launches) {
+  if (!p || nsteps < 0 || !kernel_ms || !launches) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  if (t_end != p->t_end) {
+    for (Level& L : p->levels) NS3D_CK(launch_ctrl_set_tend(L.ctrl, L.B, t_end, p->stream));
+    p->t_end = t_end;
+  }
+  KernelTimer tm;
+  for (int i = 0; i < 7; ++i) NS3D_CK(cudaEventCreate(&tm.ev[i]));
+  ns3d_status st = NS3D_OK;
+  for (int n = 0; n < nsteps && st == NS3D_OK; ++n) {
+    for (Level& L : p->levels) {
+      for (int stage = 1; stage <= 3 && st == NS3D_OK; ++stage) {
+        if (p->dtype == NS3D_F32) {
+          cplx<float>* U0 = static_cast<cplx<float>*>(L.U0);
+          cplx<float>* US = static_cast<cplx<float>*>(L.US);
+          st = enqueue_stage<float>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US,
+                                    stage == 1 && p->prm.dt_fixed <= 0, p->stream, &tm);
+        } else {
+          cplx<double>* U0 = static_cast<cplx<double>*>(L.U0);
+          cplx<double>* US = static_cast<cplx<double>*>(L.US);
+          st = enqueue_stage<double>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US,
+                                     stage == 1 && p->prm.dt_fixed <= 0, p->stream, &tm);
+        }
+        if (st != NS3D_OK) break;
+        if (cudaEventSynchronize(tm.ev[6]) != cudaSuccess) { st = NS3D_ERR_CUDA; break; }
+        for (int k = 0; k < 6; ++k) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, tm.ev[k], tm.ev[k + 1]) != cudaSuccess) { st = NS3D_ERR_CUDA; break; }
+          kernel_ms[k] += ms;
+          launches[k] += 1;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(tm.ev[i]);
+  return st;
+}

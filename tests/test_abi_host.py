@@ -1,0 +1,139 @@
+"""Host-side checks of the library boundary (no GPU needed):
+* libns3d.so builds, loads and exports every function include/ns3d.h declares;
+* argument validation and the no-device error path return status codes;
+* the CPU emulation of the kernels' block bodies (same source as the CUDA
+  kernels, one emulated thread per block) matches the oracle: this pins the
+  index logic -- strides, tiles, ragged tails, padding and truncation maps, the
+  two-for-one real transforms, radix plans -- before any GPU run."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import ns3d_inputs as I
+from oracle import solver as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2401_09843_gb300 import build
+    build.build_all()
+    return build
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "ns3d.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ns3d_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_header_function(built):
+    from paper_2401_09843_gb300 import binding
+    lib = binding.load()
+    names = header_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.SYMBOLS) == names
+
+
+def test_status_strings_and_defaults(built):
+    from paper_2401_09843_gb300 import binding
+    lib = binding.load()
+    assert lib.ns3d_status_string(0) == b"ok"
+    assert lib.ns3d_status_string(7) == b"not supported"
+    p = binding.default_params()
+    assert abs(p.L - 2 * np.pi) < 1e-15 and p.s == 1.5 and p.theta == 0.5 and p.cfl == 0.5
+
+
+def test_invalid_arguments_are_rejected(built):
+    from paper_2401_09843_gb300 import binding
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    p = binding.default_params()
+    ok = (ctypes.c_int * 1)(32)
+    for bad in ([7], [0], [2], [-8]):
+        arr = (ctypes.c_int * 1)(*bad)
+        assert lib.ns3d_plan_create(ctypes.byref(h), arr, 1, 0, ctypes.byref(p), None, 0) == 1
+    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 0, 0, ctypes.byref(p), None, 0) == 1
+    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 5, ctypes.byref(p), None, 0) == 1
+    q = binding.default_params(nonlinear_form=1)
+    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 7
+    q = binding.default_params(n_pad=40)              # below 3N/2 = 48: would alias
+    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 1
+    q = binding.default_params(cfl=0.0)
+    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 1
+    assert lib.ns3d_step(None, 1, 0.0) == 1
+    assert lib.ns3d_set_initial(None, 0, None, 0) == 1
+
+
+def test_no_device_returns_cuda_error(built):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2401_09843_gb300 import binding
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    p = binding.default_params()
+    arr = (ctypes.c_int * 1)(32)
+    assert lib.ns3d_plan_create(ctypes.byref(h), arr, 1, 0, ctypes.byref(p), None, 0) == 3
+
+
+# --------------------------------------------------------------------------- CPU emulation
+
+def hostcheck(built, uh, P, prm, nsteps=0, dt=0.0, dtype=1):
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_run.restype = ctypes.c_int
+    cd = np.complex128 if dtype == 1 else np.complex64
+    uin = np.ascontiguousarray(uh.astype(cd))
+    uout = np.zeros_like(uin)
+    p = np.array([prm.L, prm.nu, prm.s, prm.theta, prm.eps0, prm.mN_coef, prm.q_form, prm.cfl])
+    t = ctypes.c_double(0)
+    rc = lib.ns3d_hostcheck_run(dtype, uh.shape[-2], P, p.ctypes.data_as(ctypes.c_void_p),
+                                uin.ctypes.data_as(ctypes.c_void_p), uout.ctypes.data_as(ctypes.c_void_p),
+                                nsteps, ctypes.c_double(dt), ctypes.byref(t))
+    return uout, rc, t.value
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+@pytest.mark.parametrize("N,P", [(8, 12), (10, 15), (12, 18), (16, 24), (16, 32), (20, 30),
+                                 (24, 36), (22, 35), (28, 42), (32, 48), (40, 60)])
+def test_emulated_kernels_rhs_matches_oracle(built, N, P):
+    prm = S.Params(nu=0.01, eps0=1.0, L=5.0)
+    uh = I.random_spectrum(N, seed=N, k0=2.5)
+    ref = S.rhs(uh, prm, P=P)
+    got, rc, _ = hostcheck(built, uh, P, prm)
+    assert rc == 0
+    assert rel(got, ref) < 1e-13
+    got32, _, _ = hostcheck(built, uh, P, prm, dtype=0)
+    assert rel(got32, ref) < 2e-6
+
+
+def test_emulated_kernels_steps_match_oracle(built):
+    N, P = 16, 24
+    prm = S.Params(nu=0.01, eps0=1.0, q_form=1)
+    uh = I.random_spectrum(N, seed=3, k0=2.5)
+    ref, _, _ = S.integrate(uh, prm.with_(dt_fixed=0.01), 3, P=P)
+    got, rc, t = hostcheck(built, uh, P, prm, nsteps=3, dt=0.01)
+    assert rc == 0 and abs(t - 0.03) < 1e-15
+    assert rel(got, ref) < 1e-13
+    # CFL step: the emulated kernels and the oracle take the same dt sequence
+    ref, tref, _ = S.integrate(uh, prm, 2, P=P)
+    got, rc, t = hostcheck(built, uh, P, prm, nsteps=2, dt=0.0)
+    assert abs(t - tref) < 1e-14 and rel(got, ref) < 1e-12
+
+
+def test_radix_plans(built):
+    lib = ctypes.CDLL(built.HOSTLIB)
+    r = (ctypes.c_int * 8)()
+    for n in (12, 15, 48, 96, 192, 384, 768, 1152, 1536, 35, 49, 1000):
+        k = lib.ns3d_hostcheck_plan(n, r, 8)
+        assert k > 0 and int(np.prod([r[i] for i in range(k)])) == n
+    assert lib.ns3d_hostcheck_plan(22, r, 8) == -1           # prime factor 11
