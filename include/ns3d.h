@@ -196,6 +196,23 @@ ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);
 ns3d_status ns3d_step_timed(ns3d_plan plan, int nsteps, double t_end, double* kernel_ms,
                             int* launches);
 
+/* Allocation-free right-hand side for small grids (the paper has no
+ * counterpart; it is a service for callers that may not allocate device
+ * memory when they need the derivative, e.g. code running inside another
+ * component's CUDA graph capture or hosts with a memory budget fixed at start-up).
+ * Computes the same R(u_hat) as ns3d_eval_rhs without a plan: uhat and
+ * rhs_out are device buffers of the current device in D1 layout and `dtype`,
+ * all work is enqueued on cuda_stream (a cudaStream_t) and nothing waits.
+ * Every intermediate array lives in one 8 MiB file-scope device array of the
+ * library (held by every GPU that loads it until exit); no cudaMalloc or other
+ * allocation happens.  Limits: 4 <= N <= 32 and padded size P <= 48, else
+ * NS3D_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race;
+ * order them on one stream. */
+ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d_params* p,
+                                  const void* uhat, void* rhs_out, void* cuda_stream);
+
 /* Static text for a status code. */
 const char* ns3d_status_string(ns3d_status s);
 

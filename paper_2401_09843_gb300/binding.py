@@ -25,7 +25,8 @@ STATUS = {0: "NS3D_OK", 1: "NS3D_ERR_INVALID_ARG", 2: "NS3D_ERR_OUT_OF_MEMORY",
 SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d_plan_info",
            "ns3d_set_initial", "ns3d_get_state", "ns3d_step", "ns3d_synchronize",
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
-           "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed"]
+           "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
+           "ns3d_eval_rhs_noalloc"]
 
 
 class Ns3dError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         "ns3d_ensemble_stats": (i, [vp, i, ctypes.POINTER(Stats)]),
         "ns3d_status_string": (ctypes.c_char_p, [i]),
         "ns3d_step_timed": (i, [vp, i, d, ctypes.POINTER(d), ip]),
+        "ns3d_eval_rhs_noalloc": (i, [i, i, ctypes.POINTER(Params), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -97,6 +99,20 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def eval_rhs_noalloc(uhat, dtype: int = NS3D_F64, params: Params | None = None, stream=None):
+    """R(u_hat) through ns3d_eval_rhs_noalloc (no plan, no device allocation in
+    the library; N <= 32).  uhat: CUDA tensor in D1 layout of the dtype."""
+    import torch
+    lib = load()
+    p = params if params is not None else default_params()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = torch.empty_like(uhat)
+    _check(lib.ns3d_eval_rhs_noalloc(int(uhat.shape[-2]), dtype, ctypes.byref(p),
+                                     ctypes.c_void_p(uhat.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(s.cuda_stream)), "ns3d_eval_rhs_noalloc")
+    return out
 
 
 class Plan:
