@@ -9,8 +9,12 @@
 #include <vector>
 
 #include "ns3d_geom.h"
+#include "ns3d_zfast.cuh"
+#include "ns3d_colfast.cuh"
 
 namespace {
+
+bool g_use_fast = true;
 
 struct HostSync {
   void operator()() const {}
@@ -40,8 +44,31 @@ void compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N) {
               z < h ? u[(((long long)c * N + x) * N + y) * h + z] : czero<T>();
 }
 
+template <typename T, int SIGN, int N1, int N2>
+void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
+  using S = ColFastShape<N1, N2>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  const int gx = (a.ncols + S::W - 1) / S::W;
+  for (int z = 0; z < L.gz; ++z)
+    for (int y = 0; y < L.gy; ++y)
+      for (int x = 0; x < gx; ++x) {
+        colfast_twiddles<T, SIGN, N1, N2>(sm.data(), a.tw, 0, 1);
+        colfast_pass1<T, SIGN, N1, N2>(a, x, y, z, 0, 1, sm.data(), sm.data() + S::P);
+        colfast_pass2<T, SIGN, N1, N2>(a, x, y, z, 0, 1, sm.data() + S::P);
+      }
+}
+
 template <typename T, int SIGN, bool CF1, bool CFL>
 void run_col(const ColArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
+  if (g_use_fast && sizeof(T) == 4 && a.W == 16) {
+#define NS3D_HC_CF(A, B)                        \
+    if (a.pl.n == (A) * (B)) {                  \
+      run_colfast<T, SIGN, A, B>(a, L);         \
+      return;                                   \
+    }
+    NS3D_FOR_COLFAST(NS3D_HC_CF)
+#undef NS3D_HC_CF
+  }
   for (int z = 0; z < L.gz; ++z)
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < L.gx; ++x)
@@ -56,6 +83,46 @@ void run_z(const ZArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
       for (int x = 0; x < L.gx; ++x) zfused_block<T>(a, x, y, z, 0, 1, sm.data(), red, HostSync{});
 }
 
+// The register-resident z pass, phase by phase and thread by thread.
+template <typename T, int N1, int N2>
+void run_zfast(const ZArgs<T>& a, int nm) {
+  using S = ZFastShape<N1, N2>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<double> red(S::NTHR);
+  std::vector<ZFastState<T, N1, N2>> st(S::NTHR);
+  const int gx = (S::P + S::Y - 1) / S::Y;
+  for (int bz = 0; bz < nm; ++bz)
+    for (int by = 0; by < S::P; ++by)
+      for (int bx = 0; bx < gx; ++bx) {
+        ZFastCtx<T, N1, N2> c = zfast_ctx<T, N1, N2>(a, bx, by, bz, sm.data());
+        for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zfast_inv1(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) {
+          zfast_inv2(c, t, st[t]);
+          red[t] = st[t].bad ? -1.0 : (double)st[t].umax;
+        }
+        zfast_reduce(c, red.data(), S::NTHR);
+        for (int r = 0; r < 2; ++r) {
+          for (int t = 0; t < S::NTHR; ++t) zfast_fwd1(c, t, st[t], r);
+          for (int t = 0; t < S::NTHR; ++t) zfast_fwd2(c, t, S::NTHR);
+          for (int t = 0; t < S::NTHR; ++t) zfast_extract(c, t, S::NTHR, r);
+        }
+      }
+}
+
+template <typename T>
+bool run_z_fast_if_any(const ZArgs<T>& a, int P) {
+  if (sizeof(T) != 4) return false;
+#define NS3D_HC_ZF(A, B)               \
+  if (P == (A) * (B)) {                \
+    run_zfast<T, A, B>(a, 1);          \
+    return true;                       \
+  }
+  NS3D_FOR_ZFAST(NS3D_HC_ZF)
+#undef NS3D_HC_ZF
+  return false;
+}
+
 // One evaluation of Algorithm 2 and the spectral step on member 0.
 template <typename T>
 void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cplx<T>* u0,
@@ -64,9 +131,12 @@ void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cpl
                std::vector<cplx<T>>& sm) {
   using namespace ns3d;
   run_col<T, +1, true, true>(args_inv_x<T>(g, in, W1.data(), tw.data()), launch_inv_x(g, 1), sm);
-  run_col<T, +1, true, false>(args_inv_y<T>(g, W1.data(), W2.data(), tw.data()), launch_inv_y(g, 1), sm);
-  run_z<T>(args_z<T>(g, W2.data(), W1.data(), tw.data(), stage == 1 ? ctrl : nullptr), launch_z(g, 1), sm);
-  run_col<T, -1, false, true>(args_fwd_y<T>(g, W1.data(), W2.data(), tw.data()), launch_fwd_y(g, 1), sm);
+  run_col<T, +1, true, true>(args_inv_y<T>(g, W1.data(), W2.data(), tw.data()), launch_inv_y(g, 1), sm);
+  {
+    ZArgs<T> za = args_z<T>(g, W2.data(), W1.data(), tw.data(), stage == 1 ? ctrl : nullptr);
+    if (!(g_use_fast && run_z_fast_if_any<T>(za, g.P))) run_z<T>(za, launch_z(g, 1), sm);
+  }
+  run_col<T, -1, true, true>(args_fwd_y<T>(g, W1.data(), W2.data(), tw.data()), launch_fwd_y(g, 1), sm);
   run_col<T, -1, true, true>(args_fwd_x<T>(g, W2.data(), W1.data(), tw.data()), launch_fwd_x(g, 1), sm);
   SpecArgs<T> s{};
   s.bh = W1.data();
@@ -79,10 +149,11 @@ void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cpl
   s.stage = stage;
   s.m6 = g.nBh;
   s.m3 = g.nU;
-  s.sp = sp;
+  s.sp = spec_t<T>(sp);
   s.ctrl = ctrl;
-  const long long total = (long long)g.N * g.N * g.h;
-  for (long long i = 0; i < total; ++i) spectral_point<T>(s, i);
+  if (stage == 1) step_dt_member(*ctrl, sp);
+  for (int kx = 0; kx < g.N; ++kx)
+    for (int j = 0; j < g.N * g.h; ++j) spectral_point<T>(s, 0, kx, j);
 }
 
 template <typename T>
@@ -125,6 +196,9 @@ int ns3d_hostcheck_run(int dtype, int N, int P, const double* prm, const void* u
   if (dtype == 0) return run<float>(N, P, prm, uin, uout, nsteps, dt, t_out);
   return run<double>(N, P, prm, uin, uout, nsteps, dt, t_out);
 }
+
+// 0: emulate the generic tile z pass even where a register-resident one exists.
+void ns3d_hostcheck_use_fast(int on) { g_use_fast = on != 0; }
 
 // Radix plan chosen for length n (for tests).
 int ns3d_hostcheck_plan(int n, int* radix, int maxp) {

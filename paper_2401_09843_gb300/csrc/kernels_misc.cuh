@@ -12,11 +12,13 @@ static inline int grid_for(long long total, int nthr) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// grid.y = member * N + kx; threads stride over the (ky, kz) plane
 template <typename T>
-__global__ void __launch_bounds__(256) k_spectral(SpecArgs<T> a, long long total) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x)
-    spectral_point<T>(a, i);
+__global__ void __launch_bounds__(256) k_spectral(SpecArgs<T> a) {
+  const int m = blockIdx.y / a.N, kx = blockIdx.y % a.N;
+  const int plane = a.N * a.h;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < plane; j += gridDim.x * blockDim.x)
+    spectral_point<T>(a, m, kx, j);
 }
 
 // D1 [3][N][N][h+1] -> compact [3][N][N][h] with the Nyquist rows zeroed
@@ -49,8 +51,11 @@ __global__ void k_compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N) {
 }
 
 template <typename T>
-cudaError_t launch_spectral(const SpecArgs<T>& a, long long total, cudaStream_t s) {
-  k_spectral<T><<<grid_for(total, 256), 256, 0, s>>>(a, total);
+cudaError_t launch_spectral(const SpecArgs<T>& a, cudaStream_t s) {
+  const int plane = a.N * a.h;
+  int gx = (plane + 4 * 256 - 1) / (4 * 256);     // about four points per thread
+  if (gx < 1) gx = 1;
+  k_spectral<T><<<dim3(gx, a.nmem * a.N), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -66,11 +71,23 @@ cudaError_t launch_compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_zpass(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t s) {
+  if (zfast_available<T>(g.P)) {
+#define NS3D_ZF_GO(A, B) \
+    if (g.P == (A) * (B)) return zfast_launch<float, A, B>(*reinterpret_cast<const ZArgs<float>*>(&a), nm, s);
+    NS3D_FOR_ZFAST(NS3D_ZF_GO)
+#undef NS3D_ZF_GO
+  }
+  return launch_zfused<T>(a, ns3d::launch_z(g, nm), s);
+}
+
 }  // namespace ns3d
 
 #define NS3D_MISC_VARIANT(T)                                                                    \
   namespace ns3d {                                                                             \
-  template cudaError_t launch_spectral<T>(const SpecArgs<T>&, long long, cudaStream_t);        \
+  template cudaError_t launch_spectral<T>(const SpecArgs<T>&, cudaStream_t);                   \
   template cudaError_t launch_d1_to_compact<T>(const cplx<T>*, cplx<T>*, int, cudaStream_t);   \
   template cudaError_t launch_compact_to_d1<T>(const cplx<T>*, cplx<T>*, int, cudaStream_t);   \
+  template cudaError_t launch_zpass<T>(const ZArgs<T>&, const Geom&, int, cudaStream_t);      \
   }

@@ -1,0 +1,63 @@
+// Register-resident fused z pass (zfast_f32.cu): one kernel per (N1, N2).
+#pragma once
+
+#include "kernels_col.cuh"
+#include "ns3d_zfast.cuh"
+
+namespace ns3d {
+
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, 2) k_zfast(ZArgs<T> a) {
+  using S = ZFastShape<N1, N2>;
+  extern __shared__ __align__(16) unsigned char ns3d_smem[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  double* red = reinterpret_cast<double*>(sm + S::SM_ELEMS);
+  const ZFastCtx<T, N1, N2> c = zfast_ctx<T, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+  const int tid = threadIdx.x;
+  zfast_load_twiddles(c, tid, S::NTHR);
+  __syncthreads();
+  zfast_inv1(c, tid, S::NTHR);
+  __syncthreads();
+  ZFastState<T, N1, N2> st;
+  zfast_inv2(c, tid, st);
+  red[tid] = st.bad ? -1.0 : (double)st.umax;
+  __syncthreads();
+  if (tid == 0) zfast_reduce(c, red, S::NTHR);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    zfast_fwd1(c, tid, st, r);
+    __syncthreads();
+    zfast_fwd2(c, tid, S::NTHR);
+    __syncthreads();
+    zfast_extract(c, tid, S::NTHR, r);
+    __syncthreads();
+  }
+}
+
+template <typename T, int N1, int N2>
+size_t zfast_smem() {
+  using S = ZFastShape<N1, N2>;
+  return (size_t)S::SM_ELEMS * sizeof(cplx<T>) + (size_t)S::NTHR * sizeof(double);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zfast_launch(const ZArgs<T>& a, int nm, cudaStream_t s) {
+  using S = ZFastShape<N1, N2>;
+  dim3 grid((S::P + S::Y - 1) / S::Y, S::P, nm);
+  k_zfast<T, N1, N2><<<grid, S::NTHR, zfast_smem<T, N1, N2>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zfast_init() {
+  return cudaFuncSetAttribute((const void*)k_zfast<T, N1, N2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+}  // namespace ns3d
+
+#define NS3D_ZFAST_VARIANT(T, N1, N2)                                                        \
+  namespace ns3d {                                                                           \
+  template cudaError_t zfast_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);          \
+  template cudaError_t zfast_init<T, N1, N2>();                                              \
+  }

@@ -13,12 +13,23 @@ __global__ void k_ctrl_reset(Ns3dCtrl* c, int n) {
     c[i].umax_bits = 0ull;
     c[i].status = 0;
     c[i].nsteps = 0;
+    c[i].dtf = 0.f;
   }
 }
 
 __global__ void k_ctrl_set_tend(Ns3dCtrl* c, int n, double t_end) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i].t_end = t_end;
+}
+
+__global__ void k_step_dt(Ns3dCtrl* c, int n, SpecParams sp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) step_dt_member(c[i], sp);
+}
+
+cudaError_t launch_step_dt(Ns3dCtrl* c, int n, const SpecParams& sp, cudaStream_t s) {
+  k_step_dt<<<(n + 127) / 128, 128, 0, s>>>(c, n, sp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ctrl_reset(Ns3dCtrl* c, int n, cudaStream_t s) {

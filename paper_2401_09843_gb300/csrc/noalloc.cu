@@ -82,9 +82,9 @@ ns3d_status run(const Geom& g, const SpecParams& sp, const void* uhat, void* rhs
   if (cudaGetLastError() != cudaSuccess) return NS3D_ERR_CUDA;
   if (launch_d1_to_compact<T>(static_cast<const cplx<T>*>(uhat), U, g.N, s) != cudaSuccess ||
       launch_col<T>(args_inv_x<T>(g, U, W1, tw), COL_INV_CC, launch_inv_x(g, 1), s) != cudaSuccess ||
-      launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CT, launch_inv_y(g, 1), s) != cudaSuccess ||
-      launch_zfused<T>(args_z<T>(g, W2, W1, tw, nullptr), launch_z(g, 1), s) != cudaSuccess ||
-      launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_TC, launch_fwd_y(g, 1), s) != cudaSuccess ||
+      launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CC, launch_inv_y(g, 1), s) != cudaSuccess ||
+      launch_zpass<T>(args_z<T>(g, W2, W1, tw, nullptr), g, 1, s) != cudaSuccess ||
+      launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_CC, launch_fwd_y(g, 1), s) != cudaSuccess ||
       launch_col<T>(args_fwd_x<T>(g, W2, W1, tw), COL_FWD_CC, launch_fwd_x(g, 1), s) != cudaSuccess)
     return NS3D_ERR_CUDA;
   SpecArgs<T> a{};
@@ -98,9 +98,9 @@ ns3d_status run(const Geom& g, const SpecParams& sp, const void* uhat, void* rhs
   a.stage = 0;
   a.m6 = g.nBh;
   a.m3 = g.nU;
-  a.sp = sp;
+  a.sp = spec_t<T>(sp);
   a.ctrl = nullptr;
-  if (launch_spectral<T>(a, (long long)g.N * g.N * g.h, s) != cudaSuccess ||
+  if (launch_spectral<T>(a, s) != cudaSuccess ||
       launch_compact_to_d1<T>(U, static_cast<cplx<T>*>(rhs), g.N, s) != cudaSuccess)
     return NS3D_ERR_CUDA;
   return NS3D_OK;

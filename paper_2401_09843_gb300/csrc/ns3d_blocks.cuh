@@ -10,8 +10,8 @@
 //   state   U  [B][3][kx N][ky N][kz h]    retained modes; kz = N/2 is dropped,
 //                                         rows kx = h and ky = h stay zero
 //   A  (inverse x done)   [B][3][x P][ky N][kz h]
-//   Bq (inverse x,y done) [B][3][x P][kz h][y P]     y contiguous
-//   Cq (products, fwd z)  [B][6][x P][kz h][y P]
+//   Bq (inverse x,y done) [B][3][x P][y P][kz h]
+//   Cq (products, fwd z)  [B][6][x P][y P][kz h]
 //   Dq (fwd z,y)          [B][6][x P][ky N][kz h]
 //   Bh (fwd z,y,x)        [B][6][kx N][ky N][kz h]
 // The product components are ordered B00 B01 B02 B11 B12 B22.
@@ -20,6 +20,10 @@
 #include "ns3d_fft.cuh"
 
 NS3D_HD int imin(int a, int b) { return a < b ? a : b; }
+// largest finite value of T: v <= big_finite<T>() is false for NaN and +-inf
+template <typename T> NS3D_HD T big_finite();
+template <> NS3D_HD float big_finite<float>() { return 3.4028234663852886e38f; }
+template <> NS3D_HD double big_finite<double>() { return 1.7976931348623157e308; }
 NS3D_HD float xpow(float a, float b) { return powf(a, b); }
 NS3D_HD double xpow(double a, double b) { return pow(a, b); }
 
@@ -31,6 +35,8 @@ struct Ns3dCtrl {
   unsigned long long umax_bits;  // max_x sum_i |u_i| of the stage-1 field (double bits)
   int status;                    // sticky NS3D_FLAG_* bits
   int nsteps;                    // completed steps
+  float dtf;                     // dt rounded to float (read by the FP32 stage kernels)
+  int pad_;
 };
 
 #define NS3D_FLAG_NONFINITE 1
@@ -158,22 +164,23 @@ struct ZArgs {
   Ns3dCtrl* ctrl;            // per member (null: no CFL reduction)
 };
 
-// u_a + i u_b packed spectrum from the stored half spectra (row q, column col)
+// u_a + i u_b packed spectrum at position p of a length-P line, from the
+// stored half spectra of lines ca and cb (line c, wavenumber q at c*h + q)
 template <typename T>
 NS3D_HD cplx<T> pack2(const cplx<T>* ia, const cplx<T>* ib, int P, int h, int p, int ca, int cb,
                       int ncol) {
   cplx<T> a = czero<T>(), b = czero<T>();
   if (p < h) {
-    if (ca < ncol) a = ia[p * P + ca];
-    if (cb < ncol) b = ib[p * P + cb];
+    if (ca < ncol) a = ia[ca * h + p];
+    if (cb < ncol) b = ib[cb * h + p];
     if (p == 0) {
       a.y = T(0);   // a real line has a real mean: keep the Hermitian part
       b.y = T(0);
     }
   } else if (p > P - h) {
     const int q = P - p;
-    if (ca < ncol) a = cconj(ia[q * P + ca]);
-    if (cb < ncol) b = cconj(ib[q * P + cb]);
+    if (ca < ncol) a = cconj(ia[ca * h + q]);
+    if (cb < ncol) b = cconj(ib[cb * h + q]);
   } else {
     return czero<T>();
   }
@@ -228,30 +235,31 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
   cplx<T>* U2 = sm + P * ldw;
   cplx<T>* A = sm + 2 * P * ldw;
   cplx<T>* B = sm + 3 * P * ldw;
-  const cplx<T>* in = a.in + bz * a.in_bs + by * a.xs + y0;
+  const cplx<T>* in = a.in + bz * a.in_bs + by * a.xs + (long long)y0 * h;
   SmemIO<T> u01{U01, ldw}, u2s{U2, ldw};
 
-  // inverse: (u0 + i u1) per column, and u2 of columns (m, m + W/2) per pair
+  // inverse: (u0 + i u1) per column, and u2 of columns (m, m + W/2) per pair;
+  // lines are contiguous along kz, so the first pass maps positions fastest
   ZLoadInv<T> l01{in, in + a.in_cs, P, h, ncol, 0};
-  fft_tile<T, +1, true, true>(a.pl, ncol, tid, nthr, a.tw, l01, u01, A, B, ldw, sync);
+  fft_tile<T, +1, false, true>(a.pl, ncol, tid, nthr, a.tw, l01, u01, A, B, ldw, sync);
   sync();
   ZLoadInv<T> l22{in + 2 * a.in_cs, in + 2 * a.in_cs, P, h, ncol, half};
-  fft_tile<T, +1, true, true>(a.pl, half, tid, nthr, a.tw, l22, u2s, A, B, ldw, sync);
+  fft_tile<T, +1, false, true>(a.pl, half, tid, nthr, a.tw, l22, u2s, A, B, ldw, sync);
   sync();
 
   ZPhys<T> ph{U01, U2, ldw, half};
   if (a.ctrl) {
-    double m = 0.0;
+    T m = T(0);
     int bad = 0;
     for (int w = tid; w < P * ncol; w += nthr) {
       const int col = w % ncol, p = w / ncol;
       T u0, u1, u2;
       ph.get(col, p, u0, u1, u2);
-      const double s = fabs((double)u0) + fabs((double)u1) + fabs((double)u2);
-      if (!(s <= 1.0e300)) bad = 1;
-      else if (s > m) m = s;
+      const T s = fabs(u0) + fabs(u1) + fabs(u2);
+      if (!(s <= big_finite<T>())) bad = 1;
+      else m = s > m ? s : m;
     }
-    red[tid] = bad ? -1.0 : m;
+    red[tid] = bad ? -1.0 : (double)m;
     sync();
     if (tid == 0) {
       double mm = 0.0;
@@ -266,7 +274,7 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
   }
 
   // forward: three packed pairs of products, each truncated to kz < h
-  cplx<T>* out = a.out + bz * a.out_bs + by * a.xs + y0;
+  cplx<T>* out = a.out + bz * a.out_bs + by * a.xs + (long long)y0 * h;
   for (int pair = 0; pair < 3; ++pair) {
     ZLoadProd<T> lp{ph, pair};
     cplx<T>* E = fft_free_buffer(a.pl.npass, A, B);
@@ -276,13 +284,13 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
     cplx<T>* oa = out + (2 * pair) * a.out_cs;
     cplx<T>* ob = out + (2 * pair + 1) * a.out_cs;
     for (int w = tid; w < h * ncol; w += nthr) {
-      const int col = w % ncol, k = w / ncol;
+      const int k = w % h, col = w / h;
       const cplx<T> zk = E[k * ldw + col];
       const cplx<T> zm = cconj(E[((P - k) % P) * ldw + col]);
       const cplx<T> s = zk + zm;
       const cplx<T> d = zk - zm;
-      oa[k * P + col] = cmake(T(0.5) * s.x, T(0.5) * s.y);
-      ob[k * P + col] = cmake(T(0.5) * d.y, T(-0.5) * d.x);   // d / (2i)
+      oa[col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+      ob[col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);   // d / (2i)
     }
     sync();
   }
@@ -301,18 +309,6 @@ struct SpecParams {
   double cfl, dx, dt_fixed, lam_max;
 };
 
-template <typename T>
-struct SpecArgs {
-  const cplx<T>* bh;   // Bh
-  const cplx<T>* u0;   // U at t_n
-  const cplx<T>* us;   // stage state (stages 2, 3)
-  cplx<T>* out;        // next stage / next state / R (stage 0)
-  int N, h, nmem;
-  int stage;           // 0: out = R; 1, 2, 3: RK3 stages
-  long long m6, m3;    // member strides of Bh and of U
-  SpecParams sp;
-  Ns3dCtrl* ctrl;
-};
 
 NS3D_HD double member_dt(const Ns3dCtrl& c, const SpecParams& sp) {
   double dt;
@@ -328,46 +324,86 @@ NS3D_HD double member_dt(const Ns3dCtrl& c, const SpecParams& sp) {
   return dt;
 }
 
+// Start of a step for member m (one thread per member, before the stage-1
+// spectral kernel): the step's dt from the CFL maximum of the stage-1 field,
+// and the stability check lambda_max dt <= 2.5.
+NS3D_HD void step_dt_member(Ns3dCtrl& c, const SpecParams& sp) {
+  const double dt = member_dt(c, sp);
+  c.dt = dt;
+  c.dtf = (float)dt;
+  if (dt * sp.lam_max > 2.5) c.status |= NS3D_FLAG_UNSTABLE;
+}
+
+// The spectral parameters in the arithmetic type, converted once per thread.
 template <typename T>
-NS3D_HD T lambda_k(int k2, const SpecParams& sp) {
-  const T kap2 = T(sp.kscale * sp.kscale) * T(k2);
-  T lam = T(sp.nu) * kap2;
+struct SpecT {
+  T kscale, nu, epsN, s, mN2, qexp, inv_P3;
+  int kthr, q_form;
+};
+
+template <typename T>
+NS3D_HD SpecT<T> spec_t(const SpecParams& sp) {
+  SpecT<T> r;
+  r.kscale = (T)sp.kscale;
+  r.nu = (T)sp.nu;
+  r.epsN = (T)sp.epsN;
+  r.s = (T)sp.s;
+  r.mN2 = (T)sp.mN2;
+  r.qexp = (T)sp.qexp;
+  r.inv_P3 = (T)sp.inv_P3;
+  r.kthr = sp.kthr;
+  r.q_form = sp.q_form;
+  return r;
+}
+
+template <typename T>
+NS3D_HD T lambda_k(int k2, const SpecT<T>& sp) {
+  const T kap2 = sp.kscale * sp.kscale * T(k2);
+  T lam = sp.nu * kap2;
   if (k2 > sp.kthr) {
     T q = T(1);
-    if (sp.q_form == 0) q = T(1) - xpow((T)(sp.mN2 / (double)k2), (T)sp.qexp);
-    lam += T(sp.epsN) * xpow(kap2, (T)sp.s) * q;
+    if (sp.q_form == 0) q = T(1) - xpow(sp.mN2 / T(k2), sp.qexp);
+    lam += sp.epsN * xpow(kap2, sp.s) * q;
   }
   return lam;
 }
 
-// One thread per (member, kx, ky, kz); `i` is the flat index.
 template <typename T>
-NS3D_HD void spectral_point(const SpecArgs<T>& a, long long i) {
+struct SpecArgs {
+  const cplx<T>* bh;   // Bh
+  const cplx<T>* u0;   // U at t_n
+  const cplx<T>* us;   // stage state (stages 2, 3)
+  cplx<T>* out;        // next stage / next state / R (stage 0)
+  int N, h, nmem;
+  int stage;           // 0: out = R; 1, 2, 3: RK3 stages (dt from ctrl)
+  long long m6, m3;    // member strides of Bh and of U
+  SpecT<T> sp;         // parameters in the arithmetic type
+  Ns3dCtrl* ctrl;
+};
+
+template <typename T> NS3D_HD T ctrl_dt(const Ns3dCtrl& c);
+template <> NS3D_HD float ctrl_dt<float>(const Ns3dCtrl& c) { return c.dtf; }
+template <> NS3D_HD double ctrl_dt<double>(const Ns3dCtrl& c) { return c.dt; }
+
+// One thread per (member m, kx, ky, kz); j = ky * h + kz indexes the plane.
+template <typename T>
+NS3D_HD void spectral_point(const SpecArgs<T>& a, int m, int kx, int j) {
+  const SpecT<T>& sp = a.sp;
   const int h = a.h, N = a.N;
-  const int kz = (int)(i % h);
-  const int ky = (int)((i / h) % N);
-  const int kx = (int)((i / ((long long)h * N)) % N);
-  const int m = (int)(i / ((long long)h * N * N));
-  const long long off = (long long)(kx * N + ky) * h + kz;
+  const int kz = j % h;
+  const int ky = j / h;
+  const long long off = (long long)kx * N * h + j;
   const long long plane = (long long)N * N * h;
   const cplx<T>* u0 = a.u0 + m * a.m3 + off;
   cplx<T>* out = a.out + m * a.m3 + off;
 
-  double dt = 0.0;
+  T dt = T(0);
   if (a.stage >= 1) {
     Ns3dCtrl& c = a.ctrl[m];
-    if (a.stage == 1) {
-      dt = member_dt(c, a.sp);
-      if (off == 0) {
-        c.dt = dt;
-        if (dt * a.sp.lam_max > 2.5) c.status |= NS3D_FLAG_UNSTABLE;
-      }
-    } else {
-      dt = c.dt;
-    }
-    if (dt <= 0.0) {   // member finished: stages leave it unchanged
+    dt = ctrl_dt<T>(c);
+    if (!(dt > T(0))) {   // member finished: stages leave it unchanged
       if (out != u0)
-        for (int j = 0; j < 3; ++j) out[j * plane] = u0[j * plane];
+        for (int q = 0; q < 3; ++q) out[q * plane] = u0[q * plane];
       if (a.stage == 3 && off == 0) c.umax_bits = 0ull;
       return;
     }
@@ -381,11 +417,9 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, long long i) {
     R[0] = R[1] = R[2] = czero<T>();
   } else {
     const cplx<T>* bh = a.bh + m * a.m6 + off;
-    const T ks = T(a.sp.kscale);
-    const T kx_ = ks * T(sx), ky_ = ks * T(sy), kz_ = ks * T(kz);
-    const T sc = T(a.sp.inv_P3);
+    const T kx_ = sp.kscale * T(sx), ky_ = sp.kscale * T(sy), kz_ = sp.kscale * T(kz);
     cplx<T> b6[6];
-    for (int c = 0; c < 6; ++c) b6[c] = sc * bh[c * plane];
+    for (int q = 0; q < 6; ++q) b6[q] = sp.inv_P3 * bh[q * plane];
     // kappa . B_j  (B symmetric: 00 01 02 11 12 22)
     const cplx<T> t0 = kx_ * b6[0] + ky_ * b6[1] + kz_ * b6[2];
     const cplx<T> t1 = kx_ * b6[1] + ky_ * b6[3] + kz_ * b6[4];
@@ -394,7 +428,7 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, long long i) {
     const cplx<T> bb[3] = {cmake(t0.y, -t0.x), cmake(t1.y, -t1.x), cmake(t2.y, -t2.x)};
     const T kap2 = kx_ * kx_ + ky_ * ky_ + kz_ * kz_;
     const cplx<T> kb = (T(1) / kap2) * (kx_ * bb[0] + ky_ * bb[1] + kz_ * bb[2]);
-    const T lam = lambda_k<T>(k2, a.sp);
+    const T lam = lambda_k<T>(k2, sp);
     // the dissipation acts on the field R is evaluated at: u_n at stages 0
     // and 1, the stage state at stages 2 and 3
     const cplx<T>* ue = (a.stage >= 2) ? a.us + m * a.m3 + off : u0;
@@ -403,23 +437,22 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, long long i) {
     R[2] = bb[2] - kz_ * kb - lam * ue[2 * plane];
   }
 
-  const T tdt = T(dt);
-  for (int j = 0; j < 3; ++j) {
-    const cplx<T> uj = u0[j * plane];
+  for (int q = 0; q < 3; ++q) {
+    const cplx<T> uj = u0[q * plane];
     cplx<T> v;
-    if (a.stage == 0) v = R[j];
-    else if (a.stage == 1) v = uj + tdt * R[j];
+    if (a.stage == 0) v = R[q];
+    else if (a.stage == 1) v = uj + dt * R[q];
     else {
-      const cplx<T> w = a.us[m * a.m3 + off + j * plane] + tdt * R[j];
+      const cplx<T> w = a.us[m * a.m3 + off + q * plane] + dt * R[q];
       if (a.stage == 2) v = T(0.75) * uj + T(0.25) * w;
       else v = T(1.0 / 3.0) * uj + T(2.0 / 3.0) * w;
     }
     if (kx == h || ky == h) v = czero<T>();
-    out[j * plane] = v;
+    out[q * plane] = v;
   }
   if (a.stage == 3 && off == 0) {
     Ns3dCtrl& c = a.ctrl[m];
-    c.t += dt;
+    c.t += c.dt;
     c.nsteps += 1;
     c.umax_bits = 0ull;
   }

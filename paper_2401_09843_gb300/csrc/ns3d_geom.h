@@ -129,7 +129,7 @@ ColArgs<T> args_inv_x(const Geom& g, const cplx<T>* in, cplx<T>* out, const cplx
   return a;
 }
 
-// Inverse y: A [m][3][P][N][h] -> Bq [m][3][P][h][P]
+// Inverse y: A [m][3][P][N][h] -> Bq [m][3][P][P][h]
 template <typename T>
 ColArgs<T> args_inv_y(const Geom& g, const cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
   ColArgs<T> a{};
@@ -137,19 +137,19 @@ ColArgs<T> args_inv_y(const Geom& g, const cplx<T>* in, cplx<T>* out, const cplx
   a.h = g.h; a.nrow_in = g.N; a.nrow_out = g.P; a.pad_in = 1; a.trunc_out = 0;
   a.ncols = g.h; a.W = g.Wc; a.ldw = g.ldwc;
   a.in_bs = (long long)g.P * g.N * g.h; a.in_os = (long long)g.N * g.h; a.in_cs = 1; a.in_rs = g.h;
-  a.out_bs = (long long)g.P * g.h * g.P; a.out_os = (long long)g.h * g.P; a.out_cs = g.P; a.out_rs = 1;
+  a.out_bs = (long long)g.P * g.P * g.h; a.out_os = (long long)g.P * g.h; a.out_cs = 1; a.out_rs = g.h;
   a.scale = T(1);
   return a;
 }
 
-// Forward y: Cq [m][6][P][h][P] -> Dq [m][6][P][N][h]
+// Forward y: Cq [m][6][P][P][h] -> Dq [m][6][P][N][h]
 template <typename T>
 ColArgs<T> args_fwd_y(const Geom& g, const cplx<T>* in, cplx<T>* out, const cplx<T>* tw) {
   ColArgs<T> a{};
   a.in = in; a.out = out; a.tw = tw; a.pl = g.plP;
   a.h = g.h; a.nrow_in = g.P; a.nrow_out = g.N; a.pad_in = 0; a.trunc_out = 1;
   a.ncols = g.h; a.W = g.Wc; a.ldw = g.ldwc;
-  a.in_bs = (long long)g.P * g.h * g.P; a.in_os = (long long)g.h * g.P; a.in_cs = g.P; a.in_rs = 1;
+  a.in_bs = (long long)g.P * g.P * g.h; a.in_os = (long long)g.P * g.h; a.in_cs = 1; a.in_rs = g.h;
   a.out_bs = (long long)g.P * g.N * g.h; a.out_os = (long long)g.N * g.h; a.out_cs = 1; a.out_rs = g.h;
   a.scale = T(1);
   return a;
@@ -173,9 +173,9 @@ ZArgs<T> args_z(const Geom& g, const cplx<T>* in, cplx<T>* out, const cplx<T>* t
   ZArgs<T> a{};
   a.in = in; a.out = out; a.tw = tw; a.pl = g.plP;
   a.P = g.P; a.h = g.h; a.W = g.Wz; a.ldw = g.ldwz;
-  a.in_bs = g.nBq; a.in_cs = (long long)g.P * g.h * g.P;
-  a.out_bs = g.nCq; a.out_cs = (long long)g.P * g.h * g.P;
-  a.xs = (long long)g.h * g.P;
+  a.in_bs = g.nBq; a.in_cs = (long long)g.P * g.P * g.h;
+  a.out_bs = g.nCq; a.out_cs = (long long)g.P * g.P * g.h;
+  a.xs = (long long)g.P * g.h;
   a.ctrl = ctrl;
   return a;
 }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include "ns3d_geom.h"
+#include "ns3d_zfast.cuh"
+#include "ns3d_colfast.cuh"
 
 namespace ns3d {
 
@@ -13,10 +15,8 @@ namespace ns3d {
 // first / last pass (column-fast when the global data is contiguous across
 // columns, task-fast when it is contiguous along the transform axis).
 enum ColKind {
-  COL_INV_CC = 0,   // inverse, contiguous columns in and out (inverse x)
-  COL_INV_CT = 1,   // inverse, columns in, transposed out (inverse y)
-  COL_FWD_TC = 2,   // forward, transposed in, columns out (forward y)
-  COL_FWD_CC = 3,   // forward, columns in and out (forward x)
+  COL_INV_CC = 0,   // inverse, contiguous columns in and out (inverse x, inverse y)
+  COL_FWD_CC = 3,   // forward, columns in and out (forward y, forward x)
 };
 
 template <typename T, int SIGN, bool CF1, bool CFL>
@@ -24,12 +24,26 @@ cudaError_t col_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s);
 template <typename T, int SIGN, bool CF1, bool CFL>
 cudaError_t col_init();
 
+template <typename T, int SIGN, int N1, int N2>
+cudaError_t colfast_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s);
+template <typename T, int SIGN, int N1, int N2>
+cudaError_t colfast_init();
+
+// A column pass: the register-resident kernel where one exists for (T, n, tile
+// width 16), the generic tile kernel otherwise.
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaStream_t s) {
+  if (sizeof(T) == 4 && a.W == 16) {
+    const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
+#define NS3D_CF_GO(A, B)                                                          \
+    if (a.pl.n == (A) * (B))                                                      \
+      return kind == COL_INV_CC ? colfast_launch<float, +1, A, B>(af, L, s)      \
+                                : colfast_launch<float, -1, A, B>(af, L, s);
+    NS3D_FOR_COLFAST(NS3D_CF_GO)
+#undef NS3D_CF_GO
+  }
   switch (kind) {
     case COL_INV_CC: return col_launch<T, +1, true, true>(a, L, s);
-    case COL_INV_CT: return col_launch<T, +1, true, false>(a, L, s);
-    case COL_FWD_TC: return col_launch<T, -1, false, true>(a, L, s);
     case COL_FWD_CC: return col_launch<T, -1, true, true>(a, L, s);
   }
   return cudaErrorInvalidValue;
@@ -37,10 +51,32 @@ cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaS
 
 template <typename T>
 cudaError_t launch_zfused(const ZArgs<T>& a, const Launch& L, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t zfast_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t zfast_init();
+
+
+template <typename T>
+bool zfast_available(int P) {
+  if (sizeof(T) != 4) return false;
+#define NS3D_ZF_CASE(A, B) \
+  if (P == (A) * (B)) return true;
+  NS3D_FOR_ZFAST(NS3D_ZF_CASE)
+#undef NS3D_ZF_CASE
+  return false;
+}
+
+// The fused z pass of a level: the register-resident kernel where one exists
+// for (T, P), the generic tile kernel otherwise.
+template <typename T>
+cudaError_t launch_zpass(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t s);
 template <typename T>
 cudaError_t zfused_init();
 template <typename T>
-cudaError_t launch_spectral(const SpecArgs<T>& a, long long total, cudaStream_t s);
+cudaError_t launch_spectral(const SpecArgs<T>& a, cudaStream_t s);
+// per-member time step of the step starting now (before the stage-1 spectral kernel)
+cudaError_t launch_step_dt(Ns3dCtrl* c, int n, const SpecParams& sp, cudaStream_t s);
 template <typename T>
 cudaError_t launch_d1_to_compact(const cplx<T>* d1, cplx<T>* u, int N, cudaStream_t s);
 template <typename T>
@@ -48,11 +84,28 @@ cudaError_t launch_compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N, cudaStrea
 
 template <typename T>
 cudaError_t kernels_init() {
-  cudaError_t e[5] = {col_init<T, +1, true, true>(), col_init<T, +1, true, false>(),
-                      col_init<T, -1, false, true>(), col_init<T, -1, true, true>(),
+  cudaError_t e[3] = {col_init<T, +1, true, true>(), col_init<T, -1, true, true>(),
                       zfused_init<T>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
+  if (sizeof(T) == 4) {
+#define NS3D_ZF_INIT(A, B)                                  \
+    {                                                       \
+      cudaError_t r = zfast_init<float, A, B>();            \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_ZFAST(NS3D_ZF_INIT)
+#undef NS3D_ZF_INIT
+#define NS3D_CF_INIT(A, B)                                                         \
+    {                                                                              \
+      cudaError_t r1 = colfast_init<float, +1, A, B>();                            \
+      cudaError_t r2 = colfast_init<float, -1, A, B>();                            \
+      if (r1 != cudaSuccess) return r1;                                            \
+      if (r2 != cudaSuccess) return r2;                                            \
+    }
+    NS3D_FOR_COLFAST(NS3D_CF_INIT)
+#undef NS3D_CF_INIT
+  }
   return cudaSuccess;
 }
 

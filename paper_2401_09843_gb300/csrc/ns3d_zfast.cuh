@@ -1,0 +1,240 @@
+// Fused z pass with register-resident transforms, for padded sizes
+// P = N1 * N2 with both radices in registers (P = 48, 96, 192, 384).
+//
+// Same arithmetic as zfused_block (Algorithm 2 steps 2-4 along z: c2r of the
+// three velocity components with the kz padding, the six products, the CFL
+// maximum, r2c truncated to kz < N/2), organised so that each transform makes
+// a single trip through shared memory:
+//
+//   inverse, pass 1   radix N1 over positions N2*j1 + j2 (task j2), read from
+//                     global memory with the padding, twiddled, to shared memory
+//   inverse, pass 2   radix N2 (task k1): thread (pair g, k1) keeps the physical
+//                     values at positions k1 + N1*k2, k2 < N2, in registers
+//   forward, pass 1   radix N2 over the SAME positions (the forward transform
+//                     uses the transposed factorisation P = N2 * N1), products
+//                     formed in registers, twiddled, to shared memory
+//   forward, pass 2   radix N1, in place in shared memory
+//   extraction        two real lines from one complex line, truncated, stored
+//
+// A CTA holds NPAIR pairs of adjacent y columns; a pair's three inverse lines
+// are u0+iu1 of each column and u2(c)+iu2(c'), its six forward lines are
+// B00+iB01, B02+iB11, B12+iB22 of each column, done three per round.
+//
+// The kernel body is a sequence of phase functions separated by block
+// barriers; per-thread state is an explicit struct, so the CPU emulator can run
+// the phases thread by thread (hostcheck.cpp).
+#pragma once
+
+#include "ns3d_blocks.cuh"
+
+// Padded sizes with a register-resident z pass (FP32): P = N1 * N2.
+#define NS3D_FOR_ZFAST(X) X(24, 16) X(12, 16) X(12, 8) X(6, 8)
+
+template <typename T, int N1, int N2>
+struct ZFastState {
+  cplx<T> z[3][N2];   // inverse results of the pair at positions k1 + N1 k2
+  T umax;             // max of |u0| + |u1| + |u2| over the thread's points
+  int bad;
+};
+
+template <int N1, int N2>
+struct ZFastShape {
+  static constexpr int P = N1 * N2;
+  static constexpr int NPAIR = (N1 >= 24) ? 8 : 16;   // pairs per CTA
+  static constexpr int NTHR = NPAIR * N1;
+  static constexpr int Y = 2 * NPAIR;                 // columns per CTA
+  // Exchange rows are padded by one element so that the strided pass stores
+  // (stride N1 + 1 or N2 + 1 across threads) hit distinct shared-memory banks.
+  static constexpr int LP = P + (N1 > N2 ? N1 : N2);
+  // shared memory in complex elements: two twiddle tables + exchange [NPAIR][3][LP]
+  static constexpr int SM_ELEMS = 2 * P + NPAIR * 3 * LP;
+};
+
+template <typename T, int N1, int N2>
+struct ZFastCtx {
+  const ZArgs<T>* a;
+  int bx, by, bz;
+  int y0, ncol;
+  cplx<T>* twi;  // twi[k1 * N2 + j2] = exp(+2 pi i j2 k1 / P)  (inverse pass 1)
+  cplx<T>* twf;  // twf[k * N1 + k1] = exp(-2 pi i k1 k / P)    (forward pass 1)
+  cplx<T>* X;    // shared exchange buffer
+};
+
+// forward-pass exchange: natural position p = kappa + N2 k of a line
+template <int N1, int N2>
+NS3D_HD int zfast_fpos(int p) {
+  return (p / N2) * (N2 + 1) + p % N2;
+}
+
+template <typename T, int N1, int N2>
+NS3D_HD ZFastCtx<T, N1, N2> zfast_ctx(const ZArgs<T>& a, int bx, int by, int bz, cplx<T>* sm) {
+  using S = ZFastShape<N1, N2>;
+  ZFastCtx<T, N1, N2> c;
+  c.a = &a;
+  c.bx = bx;
+  c.by = by;
+  c.bz = bz;
+  c.y0 = bx * S::Y;
+  c.ncol = imin(S::Y, S::P - c.y0);
+  c.twi = sm;
+  c.twf = sm + S::P;
+  c.X = sm + 2 * S::P;
+  return c;
+}
+
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_load_twiddles(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+  for (int e = tid; e < N1 * N2; e += nthr) {
+    const int k1 = e / N2, j2 = e % N2;      // twi layout
+    cplx<T> w = c.a->tw[j2 * k1];
+    w.y = -w.y;
+    c.twi[e] = w;
+    const int k = e / N1, kk = e % N1;       // twf layout
+    c.twf[e] = c.a->tw[kk * k];
+  }
+}
+
+// inverse pass 1: tasks (pair g, line l, j2), j2 fastest for coalesced loads
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+  using S = ZFastShape<N1, N2>;
+  const ZArgs<T>& a = *c.a;
+  const int h = a.h;
+  const cplx<T>* in = a.in + c.bz * a.in_bs + c.by * a.xs + (long long)c.y0 * h;
+  for (int t = tid; t < S::NPAIR * 3 * N2; t += nthr) {
+    const int j2 = t % N2;
+    const int l = (t / N2) % 3;
+    const int g = t / (3 * N2);
+    const int ca = 2 * g + (l == 1 ? 1 : 0);
+    const int cb = 2 * g + (l == 0 ? 0 : 1);
+    const cplx<T>* ia = in + (l == 2 ? 2 : 0) * a.in_cs;
+    const cplx<T>* ib = in + (l == 2 ? 2 : 1) * a.in_cs;
+    cplx<T> v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = pack2(ia, ib, S::P, h, N2 * j1 + j2, ca, cb, c.ncol);
+    Dft<N1, +1>::run(v);
+    cplx<T>* X = c.X + (g * 3 + l) * S::LP;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      X[j2 * (N1 + 1) + k1] = (k1 == 0 || j2 == 0) ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];
+  }
+}
+
+// inverse pass 2: thread (g, k1) keeps its positions in registers
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZFastState<T, N1, N2>& st) {
+  using S = ZFastShape<N1, N2>;
+  const int k1 = tid % N1;
+  const int g = tid / N1;
+  st.umax = T(0);
+  st.bad = 0;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const cplx<T>* X = c.X + (g * 3 + l) * S::LP;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) st.z[l][j] = X[j * (N1 + 1) + k1];
+    Dft<N2, +1>::run(st.z[l]);
+  }
+  const bool va = 2 * g < c.ncol, vb = 2 * g + 1 < c.ncol;
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const T sa = fabs(st.z[0][k2].x) + fabs(st.z[0][k2].y) + fabs(st.z[2][k2].x);
+    const T sb = fabs(st.z[1][k2].x) + fabs(st.z[1][k2].y) + fabs(st.z[2][k2].y);
+    if (va) {
+      if (!(sa <= big_finite<T>())) st.bad = 1;
+      else st.umax = sa > st.umax ? sa : st.umax;
+    }
+    if (vb) {
+      if (!(sb <= big_finite<T>())) st.bad = 1;
+      else st.umax = sb > st.umax ? sb : st.umax;
+    }
+  }
+}
+
+// product line f (0..5) of the pair at register position k2:
+// column f % 2, products (00,01), (02,11), (12,22) for f / 2 = 0, 1, 2
+template <typename T, int N1, int N2>
+NS3D_HD cplx<T> zfast_product(const ZFastState<T, N1, N2>& st, int f, int k2) {
+  const int col = f & 1;
+  const T u0 = st.z[col][k2].x, u1 = st.z[col][k2].y;
+  const T u2 = col ? st.z[2][k2].y : st.z[2][k2].x;
+  const int pr = f >> 1;
+  if (pr == 0) return cmake(u0 * u0, u0 * u1);
+  if (pr == 1) return cmake(u0 * u2, u1 * u1);
+  return cmake(u1 * u2, u2 * u2);
+}
+
+// forward pass 1 of round r (lines 3r..3r+2): radix N2 over own positions
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_fwd1(const ZFastCtx<T, N1, N2>& c, int tid, const ZFastState<T, N1, N2>& st,
+                        int r) {
+  using S = ZFastShape<N1, N2>;
+  const int k1 = tid % N1;
+  const int g = tid / N1;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    cplx<T> v[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = zfast_product<T, N1, N2>(st, 3 * r + q, k2);
+    Dft<N2, -1>::run(v);
+    cplx<T>* X = c.X + (g * 3 + q) * S::LP;
+#pragma unroll
+    for (int k = 0; k < N2; ++k)
+      X[k1 * (N2 + 1) + k] = (k == 0 || k1 == 0) ? v[k] : v[k] * c.twf[k * N1 + k1];
+  }
+}
+
+// forward pass 2: radix N1 in place; tasks (g, q, kappa), kappa < N2
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+  using S = ZFastShape<N1, N2>;
+  for (int t = tid; t < S::NPAIR * 3 * N2; t += nthr) {
+    const int kap = t % N2;
+    const int line = t / N2;          // g * 3 + q
+    cplx<T>* X = c.X + line * S::LP;
+    cplx<T> v[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q) v[q] = X[q * (N2 + 1) + kap];
+    Dft<N1, -1>::run(v);
+#pragma unroll
+    for (int k = 0; k < N1; ++k) X[k * (N2 + 1) + kap] = v[k];   // position kap + N2 k
+  }
+}
+
+// extraction of round r: kz < h of two real lines from each complex line
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr, int r) {
+  using S = ZFastShape<N1, N2>;
+  const ZArgs<T>& a = *c.a;
+  const int h = a.h;
+  cplx<T>* out = a.out + c.bz * a.out_bs + c.by * a.xs + (long long)c.y0 * h;
+  for (int t = tid; t < S::NPAIR * 3 * h; t += nthr) {
+    const int k = t % h;
+    const int line = t / h;           // g * 3 + q
+    const int g = line / 3, q = line % 3;
+    const int f = 3 * r + q;
+    const int col = 2 * g + (f & 1);
+    if (col >= c.ncol) continue;
+    const cplx<T>* X = c.X + line * S::LP;
+    const cplx<T> zk = X[zfast_fpos<N1, N2>(k)];
+    const cplx<T> zm = cconj(X[zfast_fpos<N1, N2>((S::P - k) % S::P)]);
+    const cplx<T> s = zk + zm, d = zk - zm;
+    const int comp = 2 * (f >> 1);
+    out[comp * a.out_cs + col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+    out[(comp + 1) * a.out_cs + col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);
+  }
+}
+
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_reduce(const ZFastCtx<T, N1, N2>& c, const double* red, int nthr) {
+  const ZArgs<T>& a = *c.a;
+  if (!a.ctrl) return;
+  double m = 0.0;
+  int bad = 0;
+  for (int i = 0; i < nthr; ++i) {
+    if (red[i] < 0) bad = 1;
+    else if (red[i] > m) m = red[i];
+  }
+  atomic_max_u64(&a.ctrl[c.bz].umax_bits, dbl_bits(m));
+  if (bad) atomic_or_i32(&a.ctrl[c.bz].status, NS3D_FLAG_NONFINITE);
+}

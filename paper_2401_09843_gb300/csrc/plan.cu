@@ -161,12 +161,11 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
   NS3D_MARK(0);
   NS3D_CK(launch_col<T>(args_inv_x<T>(g, in, W1, tw), COL_INV_CC, launch_inv_x(g, nm), s));
   NS3D_MARK(1);
-  NS3D_CK(launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CT, launch_inv_y(g, nm), s));
+  NS3D_CK(launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CC, launch_inv_y(g, nm), s));
   NS3D_MARK(2);
-  NS3D_CK(launch_zfused<T>(args_z<T>(g, W2, W1, tw, want_umax ? L.ctrl + m0 : nullptr),
-                           launch_z(g, nm), s));
+  NS3D_CK(launch_zpass<T>(args_z<T>(g, W2, W1, tw, want_umax ? L.ctrl + m0 : nullptr), g, nm, s));
   NS3D_MARK(3);
-  NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_TC, launch_fwd_y(g, nm), s));
+  NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_CC, launch_fwd_y(g, nm), s));
   NS3D_MARK(4);
   NS3D_CK(launch_col<T>(args_fwd_x<T>(g, W2, W1, tw), COL_FWD_CC, launch_fwd_x(g, nm), s));
   NS3D_MARK(5);
@@ -181,9 +180,10 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
   a.stage = stage;
   a.m6 = g.nBh;
   a.m3 = g.nU;
-  a.sp = L.sp;
+  a.sp = spec_t<T>(L.sp);
   a.ctrl = L.ctrl + m0;
-  NS3D_CK(launch_spectral<T>(a, (long long)nm * g.N * g.N * g.h, s));
+  if (stage == 1) NS3D_CK(launch_step_dt(L.ctrl + m0, nm, L.sp, s));
+  NS3D_CK(launch_spectral<T>(a, s));
   NS3D_MARK(6);
   return NS3D_OK;
 }
@@ -351,7 +351,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     return st;
   }
   p->staging_bytes = stag;
-  p->launches_per_step = 18 * (int)p->levels.size();
+  p->launches_per_step = 19 * (int)p->levels.size();
   *out = p;
   return NS3D_OK;
 }

@@ -1,0 +1,3 @@
+// Register-resident z pass, float, P = 12 x 8.
+#include "kernels_zfast.cuh"
+NS3D_ZFAST_VARIANT(float, 12, 8)

@@ -137,3 +137,22 @@ def test_radix_plans(built):
         k = lib.ns3d_hostcheck_plan(n, r, 8)
         assert k > 0 and int(np.prod([r[i] for i in range(k)])) == n
     assert lib.ns3d_hostcheck_plan(22, r, 8) == -1           # prime factor 11
+
+
+@pytest.mark.parametrize("N,P", [(16, 48), (32, 96), (24, 192), (16, 384), (40, 96)])
+def test_emulated_register_z_pass_matches_oracle(built, N, P):
+    """The register-resident FP32 z pass (P = 48, 96, 192, 384), emulated
+    thread by thread, against the oracle; over-padding (P > 3N/2) keeps the
+    grids small while exercising every (N1, N2) shape and ragged column tiles."""
+    prm = S.Params(nu=0.01, eps0=1.0)
+    uh = I.sparse_random(N, seed=P, nmodes=24)
+    ref = S.rhs_by_convolution(uh, prm)          # the Galerkin product: independent of P
+    got32, rc, _ = hostcheck(built, uh, P, prm, dtype=0)
+    assert rc == 0 and rel(got32, ref) < 2e-6
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_use_fast(0)
+    try:
+        gen32, _, _ = hostcheck(built, uh, P, prm, dtype=0)
+    finally:
+        lib.ns3d_hostcheck_use_fast(1)
+    assert rel(gen32, ref) < 2e-6
