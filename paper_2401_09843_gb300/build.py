@@ -25,8 +25,9 @@ LIB = os.path.join(PKG, "libns3d.so")
 HOSTLIB = os.path.join(PKG, "libns3d_hostcheck.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host-only constexpr functions called from device code are errors, not warnings
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                  "-I", INCLUDE, "-I", CSRC]
+                  "--diag-error", "20013,20014,20015", "-I", INCLUDE, "-I", CSRC]
 
 
 def _nvcc() -> str:

@@ -53,14 +53,17 @@ void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < gx; ++x) {
         colfast_twiddles<T, SIGN, N1, N2>(sm.data(), a.tw, 0, 1);
-        colfast_pass1<T, SIGN, N1, N2>(a, x, y, z, 0, 1, sm.data(), sm.data() + S::P);
-        colfast_pass2<T, SIGN, N1, N2>(a, x, y, z, 0, 1, sm.data() + S::P);
+        colfast_pass1<T, SIGN, N1, N2, (SIGN > 0)>(a, x, y, z, 0, 1, sm.data(), sm.data() + S::P);
+        colfast_pass2<T, SIGN, N1, N2, (SIGN < 0)>(a, x, y, z, 0, 1, sm.data() + S::P);
       }
 }
 
 template <typename T, int SIGN, bool CF1, bool CFL>
 void run_col(const ColArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
-  if (g_use_fast && sizeof(T) == 4 && a.W == 16) {
+  const bool padded_inverse = SIGN > 0 && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
+  const bool truncated_forward = SIGN < 0 && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
+  if (g_use_fast && sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n &&
+      (padded_inverse || truncated_forward)) {
 #define NS3D_HC_CF(A, B)                        \
     if (a.pl.n == (A) * (B)) {                  \
       run_colfast<T, SIGN, A, B>(a, L);         \
@@ -112,7 +115,7 @@ void run_zfast(const ZArgs<T>& a, int nm) {
 
 template <typename T>
 bool run_z_fast_if_any(const ZArgs<T>& a, int P) {
-  if (sizeof(T) != 4) return false;
+  if (sizeof(T) != 4 || 3 * a.h != P) return false;
 #define NS3D_HC_ZF(A, B)               \
   if (P == (A) * (B)) {                \
     run_zfast<T, A, B>(a, 1);          \

@@ -14,9 +14,9 @@ __global__ void __launch_bounds__(ColFastShape<N1, N2>::NTHR) k_colfast(ColArgs<
   cplx<T>* X = tw + S::P;
   colfast_twiddles<T, SIGN, N1, N2>(tw, a.tw, threadIdx.x, S::NTHR);
   __syncthreads();
-  colfast_pass1<T, SIGN, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, S::NTHR, tw, X);
+  colfast_pass1<T, SIGN, N1, N2, (SIGN > 0)>(a, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, S::NTHR, tw, X);
   __syncthreads();
-  colfast_pass2<T, SIGN, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, S::NTHR, X);
+  colfast_pass2<T, SIGN, N1, N2, (SIGN < 0)>(a, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, S::NTHR, X);
 }
 
 template <typename T, int SIGN, int N1, int N2>

@@ -73,7 +73,7 @@ cudaError_t launch_compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N, cudaStrea
 
 template <typename T>
 cudaError_t launch_zpass(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t s) {
-  if (zfast_available<T>(g.P)) {
+  if (zfast_available<T>(g.P) && 3 * g.h == g.P) {
 #define NS3D_ZF_GO(A, B) \
     if (g.P == (A) * (B)) return zfast_launch<float, A, B>(*reinterpret_cast<const ZArgs<float>*>(&a), nm, s);
     NS3D_FOR_ZFAST(NS3D_ZF_GO)

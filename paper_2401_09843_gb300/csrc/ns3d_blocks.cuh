@@ -24,6 +24,8 @@ NS3D_HD int imin(int a, int b) { return a < b ? a : b; }
 template <typename T> NS3D_HD T big_finite();
 template <> NS3D_HD float big_finite<float>() { return 3.4028234663852886e38f; }
 template <> NS3D_HD double big_finite<double>() { return 1.7976931348623157e308; }
+NS3D_HD float xabs(float a) { return fabsf(a); }
+NS3D_HD double xabs(double a) { return fabs(a); }
 NS3D_HD float xpow(float a, float b) { return powf(a, b); }
 NS3D_HD double xpow(double a, double b) { return pow(a, b); }
 
@@ -255,7 +257,7 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
       const int col = w % ncol, p = w / ncol;
       T u0, u1, u2;
       ph.get(col, p, u0, u1, u2);
-      const T s = fabs(u0) + fabs(u1) + fabs(u2);
+      const T s = xabs(u0) + xabs(u1) + xabs(u2);
       if (!(s <= big_finite<T>())) bad = 1;
       else m = s > m ? s : m;
     }

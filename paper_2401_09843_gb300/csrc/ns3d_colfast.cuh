@@ -19,12 +19,14 @@
 
 #include "ns3d_blocks.cuh"
 
-// Transform lengths with a register-resident column pass (FP32): P = N1 * N2.
+// Transform lengths with a register-resident column pass (FP32): P = N1 * N2,
+// used with the default padding h = N/2 = P/3 (compile-time zero band).
 #define NS3D_FOR_COLFAST(X) X(24, 16) X(12, 16) X(12, 8) X(6, 8)
 
 template <int N1, int N2>
 struct ColFastShape {
   static constexpr int P = N1 * N2;
+  static constexpr int H = P / 3;        // N/2 of the default padding P = 3N/2
   static constexpr int W = 16;           // columns per CTA
   static constexpr int NTHR = 128;
   static constexpr int LP = P + 1;
@@ -40,7 +42,8 @@ NS3D_HD void colfast_twiddles(cplx<T>* tw, const cplx<T>* gtw, int tid, int nthr
   }
 }
 
-template <typename T, int SIGN, int N1, int N2>
+// PAD: the input has N = 2H rows spread over the P positions (inverse).
+template <typename T, int SIGN, int N1, int N2, bool PAD>
 NS3D_HD void colfast_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
                            const cplx<T>* tw, cplx<T>* X) {
   using S = ColFastShape<N1, N2>;
@@ -56,8 +59,14 @@ NS3D_HD void colfast_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid,
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       const int p = N2 * j1 + j2;
-      const int row = a.pad_in ? pad_row_of(p, S::P, a.h, a.nrow_in) : p;
-      v[j1] = row >= 0 ? in[col * cs + row * rs] : czero<T>();
+      if (!PAD) {
+        v[j1] = in[col * cs + p * rs];
+      } else if (pad_region(N2 * j1, N2, S::P, S::H) == PAD_ZERO) {
+        v[j1] = czero<T>();
+      } else {
+        const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
+        v[j1] = row >= 0 ? in[col * cs + row * rs] : czero<T>();
+      }
     }
     Dft<N1, SIGN>::run(v);
     cplx<T>* D = X + col * S::LP + j2 * N1;
@@ -66,7 +75,8 @@ NS3D_HD void colfast_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid,
   }
 }
 
-template <typename T, int SIGN, int N1, int N2>
+// TRUNC: only the N = 2H retained positions are stored (forward).
+template <typename T, int SIGN, int N1, int N2, bool TRUNC>
 NS3D_HD void colfast_pass2(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
                            const cplx<T>* X) {
   using S = ColFastShape<N1, N2>;
@@ -86,10 +96,14 @@ NS3D_HD void colfast_pass2(const ColArgs<T>& a, int bx, int by, int bz, int tid,
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int p = k1 + N1 * k2;
-      const int row = a.trunc_out ? pad_row_of(p, S::P, a.h, a.nrow_out) : p;
-      if (row >= 0) out[col * cs + row * rs] = a.scale * v[k2];
+      if (!TRUNC) {
+        out[col * cs + p * rs] = a.scale * v[k2];
+      } else if (pad_region(N1 * k2, N1, S::P, S::H) != PAD_ZERO) {
+        const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
+        if (row >= 0) out[col * cs + row * rs] = a.scale * v[k2];
+      }
     }
   }
-  if (a.trunc_out)   // the Nyquist row N/2 receives no position: keep it zero
-    for (int col = tid; col < ncol; col += nthr) out[col * cs + a.h * rs] = czero<T>();
+  if (TRUNC)   // the Nyquist row N/2 receives no position: keep it zero
+    for (int col = tid; col < ncol; col += nthr) out[col * cs + S::H * rs] = czero<T>();
 }

@@ -30,8 +30,10 @@
 
 #if defined(__CUDACC__)
 #define NS3D_HD __host__ __device__ __forceinline__
+#define NS3D_HDC __host__ __device__ constexpr
 #else
 #define NS3D_HD inline
+#define NS3D_HDC constexpr
 #endif
 
 template <typename T>
@@ -172,4 +174,16 @@ NS3D_HD int pad_row_of(int p, int n, int h, int nrow) {
   if (p < h) return p;
   if (p > n - h) return p - n + nrow;
   return -1;
+}
+
+// Where the positions base .. base + span - 1 of a length-n transform fall for
+// a half-width h known at compile time: all below h (kept, low rows), all in
+// the zero/dropped band h .. n - h, all above n - h (kept, high rows), or mixed.
+enum PadRegion { PAD_LOW = 0, PAD_ZERO = 1, PAD_HIGH = 2, PAD_MIXED = 3 };
+
+NS3D_HDC int pad_region(int base, int span, int n, int h) {
+  return (base + span <= h) ? PAD_LOW
+         : (base >= h && base + span - 1 <= n - h) ? PAD_ZERO
+         : (base > n - h) ? PAD_HIGH
+         : PAD_MIXED;
 }

@@ -33,7 +33,9 @@ cudaError_t colfast_init();
 // width 16), the generic tile kernel otherwise.
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaStream_t s) {
-  if (sizeof(T) == 4 && a.W == 16) {
+  const bool padded_inverse = kind == COL_INV_CC && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
+  const bool truncated_forward = kind == COL_FWD_CC && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
+  if (sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
     const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
 #define NS3D_CF_GO(A, B)                                                          \
     if (a.pl.n == (A) * (B))                                                      \

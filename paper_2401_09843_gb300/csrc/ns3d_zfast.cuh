@@ -27,7 +27,8 @@
 
 #include "ns3d_blocks.cuh"
 
-// Padded sizes with a register-resident z pass (FP32): P = N1 * N2.
+// Padded sizes with a register-resident z pass (FP32): P = N1 * N2, used with
+// the default padding h = N/2 = P/3 (compile-time zero band).
 #define NS3D_FOR_ZFAST(X) X(24, 16) X(12, 16) X(12, 8) X(6, 8)
 
 template <typename T, int N1, int N2>
@@ -40,6 +41,7 @@ struct ZFastState {
 template <int N1, int N2>
 struct ZFastShape {
   static constexpr int P = N1 * N2;
+  static constexpr int H = P / 3;                     // N/2 of the default padding P = 3N/2
   static constexpr int NPAIR = (N1 >= 24) ? 8 : 16;   // pairs per CTA
   static constexpr int NTHR = NPAIR * N1;
   static constexpr int Y = 2 * NPAIR;                 // columns per CTA
@@ -99,7 +101,7 @@ template <typename T, int N1, int N2>
 NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
   using S = ZFastShape<N1, N2>;
   const ZArgs<T>& a = *c.a;
-  const int h = a.h;
+  constexpr int h = S::H;
   const cplx<T>* in = a.in + c.bz * a.in_bs + c.by * a.xs + (long long)c.y0 * h;
   for (int t = tid; t < S::NPAIR * 3 * N2; t += nthr) {
     const int j2 = t % N2;
@@ -111,7 +113,11 @@ NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     const cplx<T>* ib = in + (l == 2 ? 2 : 1) * a.in_cs;
     cplx<T> v[N1];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) v[j1] = pack2(ia, ib, S::P, h, N2 * j1 + j2, ca, cb, c.ncol);
+    for (int j1 = 0; j1 < N1; ++j1) {
+      // positions N2 j1 .. N2 j1 + N2 - 1: the zero band is known at compile time
+      if (pad_region(N2 * j1, N2, S::P, S::H) == PAD_ZERO) v[j1] = czero<T>();
+      else v[j1] = pack2(ia, ib, S::P, S::H, N2 * j1 + j2, ca, cb, c.ncol);
+    }
     Dft<N1, +1>::run(v);
     cplx<T>* X = c.X + (g * 3 + l) * S::LP;
 #pragma unroll
@@ -138,8 +144,8 @@ NS3D_HD void zfast_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZFastState<T, N1,
   const bool va = 2 * g < c.ncol, vb = 2 * g + 1 < c.ncol;
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
-    const T sa = fabs(st.z[0][k2].x) + fabs(st.z[0][k2].y) + fabs(st.z[2][k2].x);
-    const T sb = fabs(st.z[1][k2].x) + fabs(st.z[1][k2].y) + fabs(st.z[2][k2].y);
+    const T sa = xabs(st.z[0][k2].x) + xabs(st.z[0][k2].y) + xabs(st.z[2][k2].x);
+    const T sb = xabs(st.z[1][k2].x) + xabs(st.z[1][k2].y) + xabs(st.z[2][k2].y);
     if (va) {
       if (!(sa <= big_finite<T>())) st.bad = 1;
       else st.umax = sa > st.umax ? sa : st.umax;
@@ -197,7 +203,8 @@ NS3D_HD void zfast_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     for (int q = 0; q < N1; ++q) v[q] = X[q * (N2 + 1) + kap];
     Dft<N1, -1>::run(v);
 #pragma unroll
-    for (int k = 0; k < N1; ++k) X[k * (N2 + 1) + kap] = v[k];   // position kap + N2 k
+    for (int k = 0; k < N1; ++k)   // position kap + N2 k; the truncated band is never read
+      if (pad_region(N2 * k, N2, S::P, S::H) != PAD_ZERO) X[k * (N2 + 1) + kap] = v[k];
   }
 }
 
@@ -206,7 +213,7 @@ template <typename T, int N1, int N2>
 NS3D_HD void zfast_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr, int r) {
   using S = ZFastShape<N1, N2>;
   const ZArgs<T>& a = *c.a;
-  const int h = a.h;
+  constexpr int h = S::H;
   cplx<T>* out = a.out + c.bz * a.out_bs + c.by * a.xs + (long long)c.y0 * h;
   for (int t = tid; t < S::NPAIR * 3 * h; t += nthr) {
     const int k = t % h;

@@ -139,11 +139,12 @@ def test_radix_plans(built):
     assert lib.ns3d_hostcheck_plan(22, r, 8) == -1           # prime factor 11
 
 
-@pytest.mark.parametrize("N,P", [(16, 48), (32, 96), (24, 192), (16, 384), (40, 96)])
-def test_emulated_register_z_pass_matches_oracle(built, N, P):
-    """The register-resident FP32 z pass (P = 48, 96, 192, 384), emulated
-    thread by thread, against the oracle; over-padding (P > 3N/2) keeps the
-    grids small while exercising every (N1, N2) shape and ragged column tiles."""
+@pytest.mark.parametrize("N,P", [(32, 48), (64, 96), (128, 192), (256, 384)])
+def test_emulated_register_kernels_match_oracle(built, N, P):
+    """The register-resident FP32 column and z passes (P = 48, 96, 192, 384 at
+    the default padding P = 3N/2), emulated thread by thread, against the
+    Galerkin product of a sparse field; then the generic kernels on the same
+    input."""
     prm = S.Params(nu=0.01, eps0=1.0)
     uh = I.sparse_random(N, seed=P, nmodes=24)
     ref = S.rhs_by_convolution(uh, prm)          # the Galerkin product: independent of P
