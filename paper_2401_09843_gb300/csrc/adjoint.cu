@@ -1,0 +1,346 @@
+// Discrete adjoint of the SSP-RK3 step and the gradient of a band energy
+// (not in the paper; the transpose of its right-hand side, section 2.3, and
+// of eq. RK3).  With the stages u, u1, u2 of a step and the adjoint lam of
+// its result:
+//   a2 = 2/3 (lam + dt J(u2)^T lam)
+//   a1 = 1/4 (a2 + dt J(u1)^T a2)
+//   lam_n = 1/3 lam + 3/4 a2 + a1 + dt J(u)^T a1,
+// J(u)^T w = T_N F[sum_l u_l S_jl(Leray w)] - lambda w (ns3d_blocks.cuh).
+// One evaluation of J^T: spectral prep (S from w), inverse x and y of 9
+// components (u and S), the adjoint z pass (products), forward y and x of 3
+// components, and the combine.  dt is the plan's fixed step.
+#include <vector>
+
+#include "ns3d.h"
+#include "ns3d_launch.h"
+#include "plan_internal.h"
+
+using namespace ns3d;
+
+namespace {
+
+template <typename T>
+__global__ void k_adj_prep(const cplx<T>* w, cplx<T>* S6, int N, T kscale) {
+  const int kx = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N * (N / 2); j += gridDim.x * blockDim.x)
+    adj_prep_point<T>(w, S6, N, kscale, kx, j);
+}
+
+template <typename T>
+__global__ void k_adj_combine(AdjCombineArgs<T> a) {
+  const int kx = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.N * (a.N / 2); j += gridDim.x * blockDim.x)
+    adj_combine_point<T>(a, kx, j);
+}
+
+template <typename T>
+__global__ void k_band(const cplx<T>* u, cplx<T>* out, int N, double k_lo, double k_hi) {
+  const int kx = blockIdx.y;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N * (N / 2); j += gridDim.x * blockDim.x)
+    band_point<T>(u, out, N, k_lo, k_hi, kx, j);
+}
+
+template <typename T>
+__global__ void k_zadj(ZAdjArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char ns3d_smem[];
+  zadj_block<T>(a, blockIdx.x, blockIdx.y, threadIdx.x, blockDim.x,
+                reinterpret_cast<cplx<T>*>(ns3d_smem), DevSyncS{});
+}
+
+dim3 plane_grid(int N) { return dim3((N * (N / 2) + 255) / 256, N); }
+
+// Device buffers of one adjoint computation for one member of a level.
+template <typename T>
+struct AdjWork {
+  const Geom* g = nullptr;
+  SpecParams sp{};
+  const cplx<T>* tw = nullptr;
+  double dt = 0.0;
+  std::vector<void*> mem;
+  cplx<T>* S6 = nullptr;      // S of w
+  cplx<T>* A9 = nullptr;      // 9 x P N h  (inverse x; later Cq3, Bh3)
+  cplx<T>* B9 = nullptr;      // 9 x P P h  (inverse y; later Dq3)
+  cplx<T>* W1 = nullptr;      // forward-RHS workspaces
+  cplx<T>* W2 = nullptr;
+  cplx<T>* u[3] = {};         // stage states u, u1, u2
+  cplx<T>* a2 = nullptr;
+  cplx<T>* a1 = nullptr;
+  cplx<T>* tmp = nullptr;
+  Ns3dCtrl* ctrl = nullptr;
+
+  cplx<T>* alloc(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(cplx<T>)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.push_back(q);
+    return static_cast<cplx<T>*>(q);
+  }
+  ~AdjWork() {
+    for (void* q : mem) cudaFree(q);
+  }
+  bool init(const LevelView& L, double dt_) {
+    g = L.g;
+    sp = L.sp;
+    tw = static_cast<const cplx<T>*>(L.twP);
+    dt = dt_;
+    const long long nU = g->nU;
+    S6 = alloc(2 * nU);
+    A9 = alloc((size_t)9 * g->P * g->N * g->h);
+    B9 = alloc((size_t)9 * g->P * g->P * g->h);
+    W1 = alloc(g->nW1);
+    W2 = alloc(g->nW2);
+    for (auto& x : u) x = alloc(nU);
+    a2 = alloc(nU);
+    a1 = alloc(nU);
+    tmp = alloc(nU);
+    void* c = nullptr;
+    if (cudaMalloc(&c, sizeof(Ns3dCtrl)) != cudaSuccess) return false;
+    mem.push_back(c);
+    ctrl = static_cast<Ns3dCtrl*>(c);
+    return S6 && A9 && B9 && W1 && W2 && u[0] && u[1] && u[2] && a2 && a1 && tmp;
+  }
+  StageBufs bufs(cplx<T>* u0, cplx<T>* us) const {
+    StageBufs b;
+    b.g = g;
+    b.sp = sp;
+    b.W1 = W1;
+    b.W2 = W2;
+    b.tw = tw;
+    b.u0 = u0;
+    b.us = us;
+    b.ctrl = ctrl;
+    return b;
+  }
+};
+
+#define NS3D_TRY(x)                       \
+  do {                                    \
+    ns3d_status st_ = (x);                \
+    if (st_ != NS3D_OK) return st_;       \
+  } while (0)
+#define NS3D_CUDA(x)                                  \
+  do {                                                \
+    if ((x) != cudaSuccess) return NS3D_ERR_CUDA;     \
+  } while (0)
+
+// one forward SSP-RK3 step in place on `state` (uses w.tmp as stage buffer)
+template <typename T>
+ns3d_status forward_step(AdjWork<T>& w, cplx<T>* state, cudaStream_t s) {
+  const StageBufs b = w.bufs(state, w.tmp);
+  NS3D_TRY(enqueue_rhs<T>(b, 1, 1, state, w.tmp, false, s));
+  NS3D_TRY(enqueue_rhs<T>(b, 2, 1, w.tmp, w.tmp, false, s));
+  NS3D_TRY(enqueue_rhs<T>(b, 3, 1, w.tmp, state, false, s));
+  return NS3D_OK;
+}
+
+// bh <- T_N F[sum_l u_l S_jl(Leray w)] (unnormalised), left in w.A9
+template <typename T>
+ns3d_status adjoint_products(AdjWork<T>& W, const cplx<T>* u, const cplx<T>* w, cudaStream_t s) {
+  const Geom& g = *W.g;
+  const int P = g.P, N = g.N, h = g.h;
+  k_adj_prep<T><<<plane_grid(N), 256, 0, s>>>(w, W.S6, N, (T)W.sp.kscale);
+  NS3D_CUDA(cudaGetLastError());
+  const long long nA1 = (long long)P * N * h;     // one component after inverse x
+  ColArgs<T> ax = args_inv_x<T>(g, u, W.A9, W.tw);
+  Launch lx = launch_inv_x(g, 1);                 // 3 components
+  NS3D_CUDA(launch_col<T>(ax, COL_INV_CC, lx, s));
+  ax.in = W.S6;
+  ax.out = W.A9 + 3 * nA1;
+  lx.gz = 6;
+  NS3D_CUDA(launch_col<T>(ax, COL_INV_CC, lx, s));
+  ColArgs<T> ay = args_inv_y<T>(g, W.A9, W.B9, W.tw);
+  Launch ly = launch_inv_y(g, 1);
+  ly.gz = 9;
+  NS3D_CUDA(launch_col<T>(ay, COL_INV_CC, ly, s));
+  ZAdjArgs<T> az{};
+  az.in = W.B9;
+  az.out = W.A9;
+  az.tw = W.tw;
+  az.pl = g.plP;
+  az.P = P;
+  az.h = h;
+  int Wz = 8;
+  while (Wz > 2 && (size_t)7 * P * (Wz + 1) * sizeof(cplx<T>) > 200 * 1024) Wz /= 2;
+  az.W = Wz;
+  az.ldw = Wz + 1;
+  const size_t smz = (size_t)7 * P * az.ldw * sizeof(cplx<T>);
+  NS3D_CUDA(cudaFuncSetAttribute((const void*)k_zadj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  k_zadj<T><<<dim3(cdiv(P, Wz), P), 128, smz, s>>>(az);
+  NS3D_CUDA(cudaGetLastError());
+  ColArgs<T> fy = args_fwd_y<T>(g, W.A9, W.B9, W.tw);
+  Launch lfy = launch_fwd_y(g, 1);
+  lfy.gz = 3;
+  NS3D_CUDA(launch_col<T>(fy, COL_FWD_CC, lfy, s));
+  ColArgs<T> fx = args_fwd_x<T>(g, W.B9, W.A9, W.tw);
+  Launch lfx = launch_fwd_x(g, 1);
+  lfx.gz = 3;
+  NS3D_CUDA(launch_col<T>(fx, COL_FWD_CC, lfx, s));
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status combine(AdjWork<T>& W, const cplx<T>* w, const cplx<T>* X, const cplx<T>* Y,
+                    cplx<T>* out, double alpha, double beta, double gamma, double delta,
+                    cudaStream_t s) {
+  AdjCombineArgs<T> a{};
+  a.bh = W.A9;
+  a.w = w;
+  a.X = X;
+  a.Y = Y;
+  a.out = out;
+  a.N = W.g->N;
+  a.sp = spec_t<T>(W.sp);
+  a.dt = (T)W.dt;
+  a.alpha = (T)alpha;
+  a.beta = (T)beta;
+  a.gamma = (T)gamma;
+  a.delta = (T)delta;
+  k_adj_combine<T><<<plane_grid(W.g->N), 256, 0, s>>>(a);
+  NS3D_CUDA(cudaGetLastError());
+  return NS3D_OK;
+}
+
+// lam_out = adjoint of one step at the forward state un, applied to lam3
+template <typename T>
+ns3d_status adjoint_step_c(AdjWork<T>& W, const cplx<T>* un, const cplx<T>* lam3, cplx<T>* lam_out,
+                           cudaStream_t s) {
+  const long long nU = W.g->nU;
+  NS3D_CUDA(cudaMemcpyAsync(W.u[0], un, nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+  NS3D_CUDA(launch_ctrl_reset(W.ctrl, 1, s));
+  // recompute the stages u1, u2 of the step
+  const StageBufs b1 = W.bufs(W.u[0], W.u[1]);
+  NS3D_TRY(enqueue_rhs<T>(b1, 1, 1, W.u[0], W.u[1], false, s));
+  NS3D_TRY(enqueue_rhs<T>(b1, 2, 1, W.u[1], W.u[2], false, s));
+  // a2 = 2/3 lam + 2/3 dt J(u2)^T lam
+  NS3D_TRY(adjoint_products<T>(W, W.u[2], lam3, s));
+  NS3D_TRY(combine<T>(W, lam3, nullptr, nullptr, W.a2, 2.0 / 3.0, 2.0 / 3.0, 0, 0, s));
+  // a1 = 1/4 a2 + 1/4 dt J(u1)^T a2
+  NS3D_TRY(adjoint_products<T>(W, W.u[1], W.a2, s));
+  NS3D_TRY(combine<T>(W, W.a2, nullptr, nullptr, W.a1, 0.25, 0.25, 0, 0, s));
+  // lam_n = a1 + dt J(u)^T a1 + 1/3 lam + 3/4 a2
+  NS3D_TRY(adjoint_products<T>(W, W.u[0], W.a1, s));
+  NS3D_TRY(combine<T>(W, W.a1, lam3, W.a2, lam_out, 1.0, 1.0, 1.0 / 3.0, 0.75, s));
+  return NS3D_OK;
+}
+
+size_t d1_elems(int N) { return (size_t)3 * N * N * (N / 2 + 1); }
+
+template <typename T>
+ns3d_status d1_in(const void* src, int on_device, cplx<T>* dst, int N, cplx<T>* staging, cudaStream_t s) {
+  const void* d = src;
+  if (!on_device) {
+    NS3D_CUDA(cudaMemcpyAsync(staging, src, d1_elems(N) * sizeof(cplx<T>), cudaMemcpyHostToDevice, s));
+    d = staging;
+  }
+  NS3D_CUDA(launch_d1_to_compact<T>(static_cast<const cplx<T>*>(d), dst, N, s));
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status d1_out(const cplx<T>* src, void* dst, int on_device, int N, cplx<T>* staging, cudaStream_t s) {
+  void* d = on_device ? dst : staging;
+  NS3D_CUDA(launch_compact_to_d1<T>(src, static_cast<cplx<T>*>(d), N, s));
+  if (!on_device)
+    NS3D_CUDA(cudaMemcpyAsync(dst, staging, d1_elems(N) * sizeof(cplx<T>), cudaMemcpyDeviceToHost, s));
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status adjoint_step_impl(ns3d_plan p, const LevelView& L, const void* lam1, void* lam0,
+                              const void* un, int on_device) {
+  const double dt = plan_params(p).dt_fixed;
+  if (!(dt > 0)) return NS3D_ERR_NOT_SUPPORTED;
+  cudaStream_t s = p_stream(p);
+  AdjWork<T> W;
+  if (!W.init(L, dt)) return NS3D_ERR_OUT_OF_MEMORY;
+  cplx<T>* staging = W.alloc(d1_elems(L.N));
+  cplx<T>* lin = W.alloc(W.g->nU);
+  cplx<T>* uin = W.alloc(W.g->nU);
+  cplx<T>* lo = W.alloc(W.g->nU);
+  if (!staging || !lin || !uin || !lo) return NS3D_ERR_OUT_OF_MEMORY;
+  NS3D_TRY(d1_in<T>(lam1, on_device, lin, L.N, staging, s));
+  NS3D_TRY(d1_in<T>(un, on_device, uin, L.N, staging, s));
+  NS3D_TRY(adjoint_step_c<T>(W, uin, lin, lo, s));
+  NS3D_TRY(d1_out<T>(lo, lam0, on_device, L.N, staging, s));
+  NS3D_CUDA(cudaStreamSynchronize(s));
+  return NS3D_OK;
+}
+
+template <typename T>
+ns3d_status grad_impl(ns3d_plan p, const LevelView& L, int idx, double k_lo, double k_hi,
+                      int nsteps, int C, void* grad, int on_device) {
+  const double dt = plan_params(p).dt_fixed;
+  if (!(dt > 0)) return NS3D_ERR_NOT_SUPPORTED;
+  if (C <= 0) C = 1;
+  cudaStream_t s = p_stream(p);
+  AdjWork<T> W;
+  if (!W.init(L, dt)) return NS3D_ERR_OUT_OF_MEMORY;
+  const long long nU = W.g->nU;
+  const int nck = (nsteps + C - 1) / C;
+  cplx<T>* ck = W.alloc((size_t)(nck > 0 ? nck : 1) * nU);   // checkpoints
+  cplx<T>* seg = W.alloc((size_t)C * nU);                     // states of one segment
+  cplx<T>* state = W.alloc(nU);
+  cplx<T>* lam = W.alloc(nU);
+  cplx<T>* lam2 = W.alloc(nU);
+  cplx<T>* staging = W.alloc(d1_elems(L.N));
+  if (!ck || !seg || !state || !lam || !lam2 || !staging) return NS3D_ERR_OUT_OF_MEMORY;
+  NS3D_CUDA(launch_ctrl_reset(W.ctrl, 1, s));
+  NS3D_CUDA(cudaMemcpyAsync(state, static_cast<const cplx<T>*>(L.U0) + (size_t)idx * nU,
+                            nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % C == 0)
+      NS3D_CUDA(cudaMemcpyAsync(ck + (size_t)(n / C) * nU, state, nU * sizeof(cplx<T>),
+                                cudaMemcpyDeviceToDevice, s));
+    NS3D_TRY(forward_step<T>(W, state, s));
+  }
+  // lam(T) = dJ/du(T) = u(T) on the band
+  k_band<T><<<plane_grid(L.N), 256, 0, s>>>(state, lam, L.N, k_lo, k_hi);
+  NS3D_CUDA(cudaGetLastError());
+  for (int sgi = nck - 1; sgi >= 0; --sgi) {
+    const int start = sgi * C, end = (start + C < nsteps) ? start + C : nsteps;
+    NS3D_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sgi * nU, nU * sizeof(cplx<T>),
+                              cudaMemcpyDeviceToDevice, s));
+    for (int n = start + 1; n < end; ++n) {
+      cplx<T>* dst = seg + (size_t)(n - start) * nU;
+      NS3D_CUDA(cudaMemcpyAsync(dst, dst - nU, nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+      NS3D_TRY(forward_step<T>(W, dst, s));
+    }
+    for (int n = end - 1; n >= start; --n) {
+      NS3D_TRY(adjoint_step_c<T>(W, seg + (size_t)(n - start) * nU, lam, lam2, s));
+      cplx<T>* t = lam;
+      lam = lam2;
+      lam2 = t;
+    }
+  }
+  NS3D_TRY(d1_out<T>(lam, grad, on_device, L.N, staging, s));
+  NS3D_CUDA(cudaStreamSynchronize(s));
+  return NS3D_OK;
+}
+
+}  // namespace
+
+extern "C" ns3d_status ns3d_adjoint_step(ns3d_plan p, int member, const void* lambda_np1,
+                                         void* lambda_n, const void* uhat_n, int on_device) {
+  LevelView L;
+  int idx;
+  if (!p || !lambda_np1 || !lambda_n || !uhat_n || !member_view(p, member, &L, &idx))
+    return NS3D_ERR_INVALID_ARG;
+  PlanDeviceGuard dg(p);
+  return plan_dtype(p) == NS3D_F32 ? adjoint_step_impl<float>(p, L, lambda_np1, lambda_n, uhat_n, on_device)
+                                   : adjoint_step_impl<double>(p, L, lambda_np1, lambda_n, uhat_n, on_device);
+}
+
+extern "C" ns3d_status ns3d_grad_band_energy(ns3d_plan p, int member, double k_lo, double k_hi,
+                                             int nsteps, int checkpoint_every, void* grad,
+                                             int on_device) {
+  LevelView L;
+  int idx;
+  if (!p || !grad || nsteps < 0 || !(k_hi > k_lo) || !member_view(p, member, &L, &idx))
+    return NS3D_ERR_INVALID_ARG;
+  PlanDeviceGuard dg(p);
+  return plan_dtype(p) == NS3D_F32
+             ? grad_impl<float>(p, L, idx, k_lo, k_hi, nsteps, checkpoint_every, grad, on_device)
+             : grad_impl<double>(p, L, idx, k_lo, k_hi, nsteps, checkpoint_every, grad, on_device);
+}

@@ -200,6 +200,17 @@ struct ZLoadInv {
   }
 };
 
+// (line a + i line b) of the same column; off != 0 makes b zero
+template <typename T>
+struct ZLoadInvCols {
+  const cplx<T>* ia;
+  const cplx<T>* ib;
+  int P, h, ncol, off;
+  NS3D_HD cplx<T> operator()(int col, int p) const {
+    return pack2(ia, ib, P, h, p, col, col + off, ncol);
+  }
+};
+
 template <typename T>
 struct ZPhys {  // physical velocity at (position p, column col) from the inverse results
   const cplx<T>* U01;
@@ -457,5 +468,236 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, int m, int kx, int j) {
     c.t += c.dt;
     c.nsteps += 1;
     c.umax_bits = 0ull;
+  }
+}
+
+// =====================================================================
+// Writers' statistics (section 2.4; Algorithm 1 step 3).
+// =====================================================================
+
+// round(|k|) for an integer |k|^2: the K with (2K - 1)^2 <= 4 k2 < (2K + 1)^2
+NS3D_HD int shell_of(int k2) {
+  int K = (int)sqrtf((float)k2);
+  while ((2 * K + 1) * (2 * K + 1) <= 4 * k2) ++K;
+  while (K > 0 && (2 * K - 1) * (2 * K - 1) > 4 * k2) --K;
+  return K;
+}
+
+// Inverse z pass without products: c2r of the three components of a tile
+// of y columns to the physical grid u[c][x][y][z] (real, z contiguous).
+template <typename T>
+struct ZInvArgs {
+  const cplx<T>* in;   // [3][x N][y N][kz h]
+  T* out;              // [3][x N][y N][z N]
+  const cplx<T>* tw;
+  FftPlanDev pl;       // length N
+  int N, h, W, ldw;
+};
+
+template <typename T, class Sync>
+NS3D_HD void zinv_block(const ZInvArgs<T>& a, int bx, int by, int tid, int nthr, cplx<T>* sm,
+                        const Sync& sync) {
+  const int N = a.N, h = a.h, W = a.W, ldw = a.ldw;
+  const int y0 = bx * W;
+  const int ncol = imin(W, N - y0);
+  const int half = W / 2;
+  cplx<T>* U01 = sm;
+  cplx<T>* U2 = sm + N * ldw;
+  cplx<T>* A = sm + 2 * N * ldw;
+  cplx<T>* B = sm + 3 * N * ldw;
+  const long long cstride = (long long)N * N * h;
+  const cplx<T>* in = a.in + by * (long long)N * h + (long long)y0 * h;
+  SmemIO<T> u01{U01, ldw}, u2s{U2, ldw};
+  ZLoadInv<T> l01{in, in + cstride, N, h, ncol, 0};
+  fft_tile<T, +1, false, true>(a.pl, ncol, tid, nthr, a.tw, l01, u01, A, B, ldw, sync);
+  sync();
+  ZLoadInv<T> l22{in + 2 * cstride, in + 2 * cstride, N, h, ncol, half};
+  fft_tile<T, +1, false, true>(a.pl, half, tid, nthr, a.tw, l22, u2s, A, B, ldw, sync);
+  sync();
+  ZPhys<T> ph{U01, U2, ldw, half};
+  const long long N3 = (long long)N * N * N;
+  T* out = a.out + (long long)by * N * N + (long long)y0 * N;
+  for (int w = tid; w < N * ncol; w += nthr) {
+    const int p = w % N, col = w / N;
+    T u0, u1, u2;
+    ph.get(col, p, u0, u1, u2);
+    out[col * N + p] = u0;
+    out[N3 + col * N + p] = u1;
+    out[2 * N3 + col * N + p] = u2;
+  }
+}
+
+// Welford update of the pointwise mean and co-moments with the n-th sample:
+// mean_i += d_i / n, C_ij += d_i (x_j - mean_j_new), d = x - mean_old.
+// C is stored for (i <= j) in the order 00 01 02 11 12 22.
+template <typename T>
+NS3D_HD void welford_point(const T* u, long long N3, long long i, int n, double* mean, double* C) {
+  double x[3], d[3], e[3];
+  for (int c = 0; c < 3; ++c) {
+    x[c] = (double)u[c * N3 + i];
+    d[c] = x[c] - mean[c * N3 + i];
+    mean[c * N3 + i] += d[c] / n;
+    e[c] = x[c] - mean[c * N3 + i];
+  }
+  int q = 0;
+  for (int r = 0; r < 3; ++r)
+    for (int s = r; s < 3; ++s, ++q) C[q * N3 + i] += d[r] * e[s];
+}
+
+// =====================================================================
+// Discrete adjoint (not in the paper): the transpose of the linearised RHS,
+//   J(u)^T w = T_N F[ sum_l u_l S_jl ] - lambda w,
+//   S_jl = i kappa_l w'_j + i kappa_j w'_l,  w' = Leray(w),
+// in the real inner product over the full spectrum.
+// =====================================================================
+
+// S_jl (order 00 01 02 11 12 22) of w' = Leray(w), one stored mode.
+template <typename T>
+NS3D_HD void adj_prep_point(const cplx<T>* w, cplx<T>* S6, int N, T kscale, int kx, int j) {
+  const int h = N / 2;
+  const int kz = j % h, ky = j / h;
+  const long long plane = (long long)N * N * h;
+  const long long off = (long long)kx * N * h + j;
+  const int sx = kx < h ? kx : kx - N;
+  const int sy = ky < h ? ky : ky - N;
+  const T k[3] = {kscale * T(sx), kscale * T(sy), kscale * T(kz)};
+  const T kap2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  cplx<T> wp[3];
+  if (kx == h || ky == h || kap2 == T(0)) {
+    wp[0] = wp[1] = wp[2] = czero<T>();
+  } else {
+    const cplx<T> w0 = w[off], w1 = w[plane + off], w2 = w[2 * plane + off];
+    const cplx<T> kw = (T(1) / kap2) * (k[0] * w0 + k[1] * w1 + k[2] * w2);
+    wp[0] = w0 - k[0] * kw;
+    wp[1] = w1 - k[1] * kw;
+    wp[2] = w2 - k[2] * kw;
+  }
+  int q = 0;
+  for (int r = 0; r < 3; ++r)
+    for (int s = r; s < 3; ++s, ++q) {
+      const cplx<T> t = k[s] * wp[r] + k[r] * wp[s];       // times i:
+      S6[q * plane + off] = cmake(-t.y, t.x);
+    }
+}
+
+// out = alpha w + beta dt (J^T w) + gamma X + delta Y at one stored mode, with
+// J^T w = bh / P^3 - lambda w (bh the truncated forward transform of the
+// products); Nyquist rows are zero.
+template <typename T>
+struct AdjCombineArgs {
+  const cplx<T>* bh;
+  const cplx<T>* w;
+  const cplx<T>* X;
+  const cplx<T>* Y;
+  cplx<T>* out;
+  int N;
+  SpecT<T> sp;
+  T dt, alpha, beta, gamma, delta;
+};
+
+template <typename T>
+NS3D_HD void adj_combine_point(const AdjCombineArgs<T>& a, int kx, int j) {
+  const int N = a.N, h = N / 2;
+  const int kz = j % h, ky = j / h;
+  const long long plane = (long long)N * N * h;
+  const long long off = (long long)kx * N * h + j;
+  const int sx = kx < h ? kx : kx - N;
+  const int sy = ky < h ? ky : ky - N;
+  const bool nyq = (kx == h || ky == h);
+  const T lam = lambda_k<T>(sx * sx + sy * sy + kz * kz, a.sp);
+  for (int c = 0; c < 3; ++c) {
+    const long long i = c * plane + off;
+    cplx<T> v = czero<T>();
+    if (!nyq) {
+      const cplx<T> jt = a.sp.inv_P3 * a.bh[i] - lam * a.w[i];
+      v = a.alpha * a.w[i] + (a.beta * a.dt) * jt;
+      if (a.X) v = v + a.gamma * a.X[i];
+      if (a.Y) v = v + a.delta * a.Y[i];
+    }
+    a.out[i] = v;
+  }
+}
+
+// Band mask: out = u where k_lo <= |k| < k_hi (|k| of the integer wavenumber)
+template <typename T>
+NS3D_HD void band_point(const cplx<T>* u, cplx<T>* out, int N, double k_lo, double k_hi, int kx, int j) {
+  const int h = N / 2;
+  const int kz = j % h, ky = j / h;
+  const long long plane = (long long)N * N * h;
+  const long long off = (long long)kx * N * h + j;
+  const int sx = kx < h ? kx : kx - N;
+  const int sy = ky < h ? ky : ky - N;
+  const double km = sqrt((double)(sx * sx + sy * sy + kz * kz));
+  const bool in = km >= k_lo && km < k_hi && kx != h && ky != h;
+  for (int c = 0; c < 3; ++c) out[c * plane + off] = in ? u[c * plane + off] : czero<T>();
+}
+
+// Adjoint z pass: c2r of u (3) and S (6) packed as five complex lines per
+// column -- (u0,u1) (u2,S00) (S01,S02) (S11,S12) (S22,0) -- the products
+// c_j = sum_l u_l S_jl, and r2c of (c0,c1) and (c2,0), truncated.
+template <typename T>
+struct ZAdjArgs {
+  const cplx<T>* in;   // [9][x P][y P][kz h]
+  cplx<T>* out;        // [3][x P][y P][kz h]
+  const cplx<T>* tw;
+  FftPlanDev pl;
+  int P, h, W, ldw;
+};
+
+template <typename T>
+struct ZAdjLoadProd {
+  const cplx<T>* U[5];
+  int ldw, line;   // line 0: c0 + i c1, line 1: c2
+  NS3D_HD cplx<T> operator()(int col, int p) const {
+    const int o = p * ldw + col;
+    const cplx<T> a = U[0][o], b = U[1][o], c = U[2][o], d = U[3][o], e = U[4][o];
+    const T u0 = a.x, u1 = a.y, u2 = b.x;
+    const T S00 = b.y, S01 = c.x, S02 = c.y, S11 = d.x, S12 = d.y, S22 = e.x;
+    if (line == 0) return cmake(u0 * S00 + u1 * S01 + u2 * S02, u0 * S01 + u1 * S11 + u2 * S12);
+    return cmake(u0 * S02 + u1 * S12 + u2 * S22, T(0));
+  }
+};
+
+template <typename T, class Sync>
+NS3D_HD void zadj_block(const ZAdjArgs<T>& a, int bx, int by, int tid, int nthr, cplx<T>* sm,
+                        const Sync& sync) {
+  const int P = a.P, h = a.h, W = a.W, ldw = a.ldw;
+  const int y0 = bx * W;
+  const int ncol = imin(W, P - y0);
+  const long long cs = (long long)P * P * h;
+  const cplx<T>* in = a.in + by * (long long)P * h + (long long)y0 * h;
+  cplx<T>* U[5];
+  for (int l = 0; l < 5; ++l) U[l] = sm + l * P * ldw;
+  cplx<T>* A = sm + 5 * P * ldw;
+  cplx<T>* B = sm + 6 * P * ldw;
+  const int big = 1 << 30;
+  for (int l = 0; l < 5; ++l) {
+    const cplx<T>* ia = in + (2 * l) * cs;
+    const cplx<T>* ib = in + (l < 4 ? 2 * l + 1 : 2 * l) * cs;
+    ZLoadInvCols<T> ld{ia, ib, P, h, ncol, l < 4 ? 0 : big};
+    SmemIO<T> st{U[l], ldw};
+    fft_tile<T, +1, false, true>(a.pl, ncol, tid, nthr, a.tw, ld, st, A, B, ldw, sync);
+    sync();
+  }
+  cplx<T>* out = a.out + by * (long long)P * h + (long long)y0 * h;
+  for (int line = 0; line < 2; ++line) {
+    ZAdjLoadProd<T> lp{{U[0], U[1], U[2], U[3], U[4]}, ldw, line};
+    cplx<T>* E = fft_free_buffer(a.pl.npass, A, B);
+    SmemIO<T> e{E, ldw};
+    fft_tile<T, -1, true, true>(a.pl, ncol, tid, nthr, a.tw, lp, e, A, B, ldw, sync);
+    sync();
+    for (int w = tid; w < h * ncol; w += nthr) {
+      const int k = w % h, col = w / h;
+      const cplx<T> zk = E[k * ldw + col];
+      const cplx<T> zm = cconj(E[((P - k) % P) * ldw + col]);
+      const cplx<T> s = zk + zm, d = zk - zm;
+      if (line == 0) {
+        out[col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+        out[cs + col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);
+      } else {
+        out[2 * cs + col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+      }
+    }
+    sync();
   }
 }

@@ -18,6 +18,7 @@
 
 #include "ns3d.h"
 #include "ns3d_launch.h"
+#include "plan_internal.h"
 
 using namespace ns3d;
 
@@ -140,30 +141,48 @@ ns3d_status upload_twiddles(Level& L, cudaStream_t s) {
 // One evaluation of Algorithm 2 plus the spectral step for members
 // [m0, m0 + nm) of a level.  `in` is the field R is evaluated at; stage 0
 // writes R to `out`, stages 1-3 the SSP-RK3 combinations.
-// Optional per-kernel timing: events recorded before each kernel kind.
-struct KernelTimer {
-  cudaEvent_t ev[7];
-  int kinds = 0;
-};
-
 #define NS3D_MARK(i) \
   if (tm) NS3D_CK(cudaEventRecord(tm->ev[i], s))
+
+StageBufs level_bufs(Level& L, int m0) {
+  StageBufs b;
+  b.g = &L.g;
+  b.sp = L.sp;
+  b.W1 = L.W1;
+  b.W2 = L.W2;
+  b.tw = L.twP;
+  b.u0 = static_cast<unsigned char*>(L.U0) + (size_t)m0 * L.g.nU * L.g.esz;
+  b.us = static_cast<unsigned char*>(L.US) + (size_t)m0 * L.g.nU * L.g.esz;
+  b.ctrl = L.ctrl + m0;
+  return b;
+}
 
 template <typename T>
 ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in, cplx<T>* out,
                           bool want_umax, cudaStream_t s, KernelTimer* tm = nullptr) {
-  const Geom& g = L.g;
-  cplx<T>* W1 = static_cast<cplx<T>*>(L.W1);
-  cplx<T>* W2 = static_cast<cplx<T>*>(L.W2);
-  const cplx<T>* tw = static_cast<const cplx<T>*>(L.twP);
-  cplx<T>* U0 = static_cast<cplx<T>*>(L.U0) + m0 * g.nU;
-  cplx<T>* US = static_cast<cplx<T>*>(L.US) + m0 * g.nU;
+  return enqueue_rhs<T>(level_bufs(L, m0), stage, nm, in, out, want_umax, s, tm);
+}
+
+}  // namespace
+
+// One evaluation of Algorithm 2 plus the spectral step for members [0, nm)
+// of the buffers.  `in` is the field R is evaluated at; stage 0 writes R to
+// `out`, stages 1-3 the SSP-RK3 combinations.
+template <typename T>
+ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in, cplx<T>* out,
+                        bool want_umax, cudaStream_t s, KernelTimer* tm) {
+  const Geom& g = *b.g;
+  cplx<T>* W1 = static_cast<cplx<T>*>(b.W1);
+  cplx<T>* W2 = static_cast<cplx<T>*>(b.W2);
+  const cplx<T>* tw = static_cast<const cplx<T>*>(b.tw);
+  cplx<T>* U0 = static_cast<cplx<T>*>(b.u0);
+  cplx<T>* US = static_cast<cplx<T>*>(b.us);
   NS3D_MARK(0);
   NS3D_CK(launch_col<T>(args_inv_x<T>(g, in, W1, tw), COL_INV_CC, launch_inv_x(g, nm), s));
   NS3D_MARK(1);
   NS3D_CK(launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CC, launch_inv_y(g, nm), s));
   NS3D_MARK(2);
-  NS3D_CK(launch_zpass<T>(args_z<T>(g, W2, W1, tw, want_umax ? L.ctrl + m0 : nullptr), g, nm, s));
+  NS3D_CK(launch_zpass<T>(args_z<T>(g, W2, W1, tw, want_umax ? b.ctrl : nullptr), g, nm, s));
   NS3D_MARK(3);
   NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_CC, launch_fwd_y(g, nm), s));
   NS3D_MARK(4);
@@ -180,13 +199,20 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
   a.stage = stage;
   a.m6 = g.nBh;
   a.m3 = g.nU;
-  a.sp = spec_t<T>(L.sp);
-  a.ctrl = L.ctrl + m0;
-  if (stage == 1) NS3D_CK(launch_step_dt(L.ctrl + m0, nm, L.sp, s));
+  a.sp = spec_t<T>(b.sp);
+  a.ctrl = b.ctrl;
+  if (stage == 1) NS3D_CK(launch_step_dt(b.ctrl, nm, b.sp, s));
   NS3D_CK(launch_spectral<T>(a, s));
   NS3D_MARK(6);
   return NS3D_OK;
 }
+
+template ns3d_status enqueue_rhs<float>(const StageBufs&, int, int, const cplx<float>*, cplx<float>*,
+                                        bool, cudaStream_t, KernelTimer*);
+template ns3d_status enqueue_rhs<double>(const StageBufs&, int, int, const cplx<double>*,
+                                         cplx<double>*, bool, cudaStream_t, KernelTimer*);
+
+namespace {
 
 template <typename T>
 ns3d_status enqueue_step(ns3d_plan p, cudaStream_t s) {
@@ -466,25 +492,6 @@ extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, 
   return NS3D_OK;
 }
 
-extern "C" ns3d_status ns3d_adjoint_step(ns3d_plan p, int member, const void* lambda_np1,
-                                         void* lambda_n, const void* uhat_n, int on_device) {
-  (void)p; (void)member; (void)lambda_np1; (void)lambda_n; (void)uhat_n; (void)on_device;
-  return NS3D_ERR_NOT_SUPPORTED;
-}
-
-extern "C" ns3d_status ns3d_grad_band_energy(ns3d_plan p, int member, double k_lo, double k_hi,
-                                             int nsteps, int checkpoint_every, void* grad,
-                                             int on_device) {
-  (void)p; (void)member; (void)k_lo; (void)k_hi; (void)nsteps; (void)checkpoint_every;
-  (void)grad; (void)on_device;
-  return NS3D_ERR_NOT_SUPPORTED;
-}
-
-extern "C" ns3d_status ns3d_ensemble_stats(ns3d_plan p, int level_N, ns3d_stats* out) {
-  (void)p; (void)level_N; (void)out;
-  return NS3D_ERR_NOT_SUPPORTED;
-}
-
 extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, double* kernel_ms,
                                        int* launches) {
   if (!p || nsteps < 0 || !kernel_ms || !launches) return NS3D_ERR_INVALID_ARG;
@@ -499,22 +506,29 @@ extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, do
   for (int n = 0; n < nsteps && st == NS3D_OK; ++n) {
     for (Level& L : p->levels) {
       for (int stage = 1; stage <= 3 && st == NS3D_OK; ++stage) {
+        const bool um = stage == 1 && p->prm.dt_fixed <= 0;
         if (p->dtype == NS3D_F32) {
           cplx<float>* U0 = static_cast<cplx<float>*>(L.U0);
           cplx<float>* US = static_cast<cplx<float>*>(L.US);
-          st = enqueue_stage<float>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US,
-                                    stage == 1 && p->prm.dt_fixed <= 0, p->stream, &tm);
+          st = enqueue_stage<float>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US, um,
+                                    p->stream, &tm);
         } else {
           cplx<double>* U0 = static_cast<cplx<double>*>(L.U0);
           cplx<double>* US = static_cast<cplx<double>*>(L.US);
-          st = enqueue_stage<double>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US,
-                                     stage == 1 && p->prm.dt_fixed <= 0, p->stream, &tm);
+          st = enqueue_stage<double>(L, stage, 0, L.B, stage == 1 ? U0 : US, stage == 3 ? U0 : US, um,
+                                     p->stream, &tm);
         }
         if (st != NS3D_OK) break;
-        if (cudaEventSynchronize(tm.ev[6]) != cudaSuccess) { st = NS3D_ERR_CUDA; break; }
+        if (cudaEventSynchronize(tm.ev[6]) != cudaSuccess) {
+          st = NS3D_ERR_CUDA;
+          break;
+        }
         for (int k = 0; k < 6; ++k) {
           float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, tm.ev[k], tm.ev[k + 1]) != cudaSuccess) { st = NS3D_ERR_CUDA; break; }
+          if (cudaEventElapsedTime(&ms, tm.ev[k], tm.ev[k + 1]) != cudaSuccess) {
+            st = NS3D_ERR_CUDA;
+            break;
+          }
           kernel_ms[k] += ms;
           launches[k] += 1;
         }
@@ -523,4 +537,64 @@ extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, do
   }
   for (int i = 0; i < 7; ++i) cudaEventDestroy(tm.ev[i]);
   return st;
+}
+
+// ------------------------------------------------------------ internal views
+
+namespace {
+void fill_view(const Level& L, int index, LevelView* v) {
+  v->N = L.N;
+  v->P = L.P;
+  v->B = L.B;
+  v->index = index;
+  v->g = &L.g;
+  v->U0 = L.U0;
+  v->US = L.US;
+  v->W1 = L.W1;
+  v->W2 = L.W2;
+  v->twP = L.twP;
+  v->ctrl = L.ctrl;
+  v->sp = L.sp;
+}
+}  // namespace
+
+bool find_level(ns3d_plan p, int N, LevelView* out) {
+  if (!p) return false;
+  for (size_t i = 0; i < p->levels.size(); ++i)
+    if (p->levels[i].N == N) {
+      fill_view(p->levels[i], (int)i, out);
+      return true;
+    }
+  return false;
+}
+
+bool member_view(ns3d_plan p, int member, LevelView* out, int* idx) {
+  Level* L;
+  if (member_lookup(p, member, &L, idx) != NS3D_OK) return false;
+  fill_view(*L, p->loc[member].first, out);
+  return true;
+}
+
+cudaStream_t p_stream(ns3d_plan p) { return p->stream; }
+ns3d_dtype plan_dtype(ns3d_plan p) { return p->dtype; }
+const ns3d_params& plan_params(ns3d_plan p) { return p->prm; }
+
+ns3d_status status_of_level(ns3d_plan p, const LevelView& L) {
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NS3D_ERR_CUDA;
+  std::vector<Ns3dCtrl> c(L.B);
+  if (cudaMemcpy(c.data(), L.ctrl, L.B * sizeof(Ns3dCtrl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NS3D_ERR_CUDA;
+  int flags = 0;
+  for (const Ns3dCtrl& x : c) flags |= x.status;
+  return status_of_flags(flags);
+}
+
+PlanDeviceGuard::PlanDeviceGuard(ns3d_plan p) {
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (p && prev != p->device) cudaSetDevice(p->device);
+}
+
+PlanDeviceGuard::~PlanDeviceGuard() {
+  int cur = -1;
+  if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
 }

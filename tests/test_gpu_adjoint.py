@@ -1,0 +1,110 @@
+"""GPU discrete adjoint (ns3d_adjoint_step, ns3d_grad_band_energy) against the
+oracle's pinned adjoint, central finite differences of GPU forward runs along
+seeded random divergence-free directions, and the autograd wrapper."""
+import numpy as np
+import pytest
+
+import ns3d_inputs as I
+from oracle import adjoint as A
+from oracle import solver as S
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm((np.asarray(a) - b).ravel()) / np.linalg.norm(np.asarray(b).ravel())
+
+
+@pytest.mark.parametrize("N", [12, 16])
+def test_adjoint_step_matches_oracle(lib, N):
+    from paper_2401_09843_gb300 import binding as B
+    dt = 0.04
+    prm = S.Params(nu=0.01, eps0=1.0)
+    p = B.Plan([N], B.NS3D_F64, nu=0.01, eps0=1.0, dt_fixed=dt)
+    u = I.random_spectrum(N, seed=5, k0=2.5)
+    lam = I.random_spectrum(N, seed=6, k0=3.0)
+    got = p.adjoint_step(0, lam, u).cpu().numpy()
+    ref = A.rk3_adjoint_step(u, lam, dt, prm)
+    assert rel(got, ref) < 1e-11
+    # the transpose of the (oracle) tangent step
+    du = I.random_spectrum(N, seed=7, k0=3.0)
+    lhs = S.inner(lam, A.rk3_tangent_step(u, du, dt, prm))
+    assert abs(S.inner(got, du) - lhs) < 1e-11 * abs(lhs)
+    p.close()
+
+
+def test_grad_band_energy_matches_oracle(lib):
+    from paper_2401_09843_gb300 import binding as B
+    N, dt, n = 12, 0.04, 6
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u0 = I.random_spectrum(N, seed=8, k0=2.5)
+    p = B.Plan([N], B.NS3D_F64, nu=0.01, eps0=1.0, dt_fixed=dt)
+    p.set_initial(0, u0)
+    got = p.grad_band_energy(0, 2.0, 4.0, n, checkpoint_every=4).cpu().numpy()
+    ref = A.grad_band_energy(u0, prm, n, dt, 2.0, 4.0, checkpoint_every=4)
+    assert rel(got, ref) < 1e-11
+    assert np.array_equal(p.get_state(0).cpu().numpy(), u0)     # state untouched
+    p.close()
+
+
+def _J_gpu(B, N, dtype, u, nsteps, dt, k_lo, k_hi):
+    p = B.Plan([N], dtype, eps0=1.0, dt_fixed=dt)
+    p.set_initial(0, u)
+    p.step(nsteps)
+    uT = p.get_state(0).cpu().numpy().astype(np.complex128)
+    p.close()
+    return A.band_energy(uT, k_lo, k_hi)
+
+
+@pytest.mark.parametrize("N,nsteps,C", [(32, 40, 10)])
+def test_gradient_central_differences(lib, N, nsteps, C):
+    """Band 8 <= |k| < 16 at step `nsteps`, fixed dt, checkpoints every C
+    steps: <grad, v> against central differences of GPU FP64 forward runs
+    along seeded random divergence-free directions (seeds 1..3)."""
+    from paper_2401_09843_gb300 import binding as B
+    dt = 0.01
+    u0 = I.random_spectrum(N, seed=20240004)
+    p = B.Plan([N], B.NS3D_F64, eps0=1.0, dt_fixed=dt)
+    p.set_initial(0, u0)
+    g = p.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=C).cpu().numpy()
+    p.close()
+    for seed in (1, 2, 3):
+        v = I.random_spectrum(N, seed=seed, energy=0.5)
+        h = 1e-4
+        fd = (_J_gpu(B, N, B.NS3D_F64, u0 + h * v, nsteps, dt, 8.0, 16.0)
+              - _J_gpu(B, N, B.NS3D_F64, u0 - h * v, nsteps, dt, 8.0, 16.0)) / (2 * h)
+        assert abs(S.inner(g, v) - fd) < 1e-6 * abs(fd), seed
+
+
+def test_fp32_gradient_tracks_fp64(lib):
+    from paper_2401_09843_gb300 import binding as B
+    N, dt, n = 32, 0.01, 20
+    u0 = I.random_spectrum(N, seed=20240004)
+    out = {}
+    for dt_ in (B.NS3D_F64, B.NS3D_F32):
+        p = B.Plan([N], dt_, eps0=1.0, dt_fixed=dt)
+        p.set_initial(0, u0)
+        out[dt_] = p.grad_band_energy(0, 8.0, 16.0, n, checkpoint_every=5).cpu().numpy().astype(np.complex128)
+        p.close()
+    assert rel(out[B.NS3D_F32], out[B.NS3D_F64]) < 1e-4
+
+
+def test_autograd_wrapper(lib):
+    import torch
+    from paper_2401_09843_gb300 import binding as B
+    from paper_2401_09843_gb300.autograd import band_energy
+    N, dt, n = 16, 0.02, 5
+    u0 = I.random_spectrum(N, seed=3, k0=3.0)
+    x = torch.tensor(u0, dtype=torch.complex128, device="cuda", requires_grad=True)
+    J = band_energy(x, 2.0, 5.0, n, dt, eps0=1.0)
+    (gx,) = torch.autograd.grad(J, x)
+    prm = S.Params(eps0=1.0)
+    Jref = A.band_energy(S.integrate(u0, prm.with_(dt_fixed=dt), n)[0], 2.0, 5.0)
+    assert abs(J.item() - Jref) < 1e-12 * Jref
+    g = A.grad_band_energy(u0, prm, n, dt, 2.0, 5.0)
+    w = S.half_weights(N)
+    assert rel(gx.cpu().numpy(), g * w) < 1e-11
+    # torch's convention: dJ = sum Re(conj(grad) dz) over the stored tensor
+    v = I.random_spectrum(N, seed=9, k0=3.0)
+    lhs = float(np.sum((np.conj(gx.cpu().numpy()) * v).real))
+    assert abs(lhs - S.inner(g, v)) < 1e-11 * abs(lhs)

@@ -1,0 +1,82 @@
+"""GPU ensemble statistics (ns3d_ensemble_stats) against the oracle's
+definitions, and agreement of evolved ensembles within Monte Carlo error bars."""
+import numpy as np
+import pytest
+
+import ns3d_inputs as I
+from oracle import solver as S
+from oracle import stats as T
+from paper_2401_09843_gb300.ensemble import merge_stats
+
+pytestmark = pytest.mark.gpu
+
+KEYS = [("mean", "mean"), ("second", "second"), ("var", "var"), ("spectrum", "spectrum"),
+        ("spectrum_se", "spectrum_stderr"), ("s2", "s2"), ("s2_se", "s2_stderr")]
+
+
+def _check(gpu, ref, rtol):
+    for gk, rk in KEYS:
+        a, b = np.asarray(gpu[gk]), np.asarray(ref[rk])
+        assert np.max(np.abs(a - b)) <= rtol * max(np.max(np.abs(b)), 1e-30), gk
+    assert abs(gpu["energy"] - ref["energy"]) <= rtol * ref["energy"]
+    assert abs(gpu["energy_se"] - ref["energy_stderr"]) <= rtol * max(ref["energy"], 1e-30)
+    assert gpu["members"] == ref["M"]
+
+
+@pytest.mark.parametrize("dt,rtol", [("f64", 1e-11), ("f32", 2e-6)])
+def test_stats_match_oracle(lib, dt, rtol):
+    from paper_2401_09843_gb300 import binding as B
+    dtype = B.NS3D_F64 if dt == "f64" else B.NS3D_F32
+    Ns = [16, 8, 16, 16, 8, 16, 16]          # two levels; the N = 16 level has 5 members
+    p = B.Plan(Ns, dtype, eps0=1.0)
+    u = [I.random_spectrum(n, seed=41, member=m, k0=2.5) for m, n in enumerate(Ns)]
+    for m, x in enumerate(u):
+        p.set_initial(m, x)
+    for N in (16, 8):
+        mem = [m for m, n in enumerate(Ns) if n == N]
+        ref = T.ensemble_stats(np.stack([u[m] for m in mem]), S.TWO_PI)
+        _check(p.ensemble_stats(N), ref, rtol)
+    p.close()
+
+
+def test_single_member_has_zero_errors(lib):
+    from paper_2401_09843_gb300 import binding as B
+    p = B.Plan([12], B.NS3D_F64, eps0=1.0)
+    u = I.random_spectrum(12, seed=2)
+    p.set_initial(0, u)
+    st = p.ensemble_stats(12)
+    assert st["members"] == 1 and np.all(st["var"] == 0) and np.all(st["spectrum_se"] == 0)
+    assert abs(st["energy"] - S.energy(u)) < 1e-14
+    p.close()
+
+
+def test_evolved_ensemble_within_error_bars_and_shard_merge(lib):
+    """8 random members evolved 5 CFL steps in FP32 on the GPU and in FP64 by
+    the oracle: statistics agree within 3 combined Monte Carlo standard
+    errors (here far closer: the same members); two 'virtual ranks' of 4
+    members merge (Chan) to the 8-member statistics."""
+    from paper_2401_09843_gb300 import binding as B
+    N, M = 16, 8
+    u = [I.random_spectrum(N, seed=77, member=m, k0=3.0) for m in range(M)]
+    prm = S.Params(eps0=1.0, cfl=0.5)
+    p = B.Plan([N] * M, B.NS3D_F32, eps0=1.0, cfl=0.5)
+    for m in range(M):
+        p.set_initial(m, u[m])
+    p.step(5)
+    g = p.ensemble_stats(N)
+    ref = T.ensemble_stats(np.stack([S.integrate(x, prm, 5)[0] for x in u]), S.TWO_PI)
+    comb = np.sqrt(np.asarray(g["spectrum_se"]) ** 2 + ref["spectrum_stderr"] ** 2)
+    assert np.all(np.abs(np.asarray(g["spectrum"]) - ref["spectrum"]) <= 3 * comb + 1e-12)
+    assert abs(g["energy"] - ref["energy"]) <= 3 * np.hypot(g["energy_se"], ref["energy_stderr"])
+    halves = []
+    for part in (u[:4], u[4:]):
+        q = B.Plan([N] * 4, B.NS3D_F32, eps0=1.0, cfl=0.5)
+        for m, x in enumerate(part):
+            q.set_initial(m, x)
+        q.step(5)
+        halves.append(q.ensemble_stats(N))
+        q.close()
+    merged = merge_stats(halves[0], halves[1])
+    for k in ("mean", "second", "var", "spectrum", "spectrum_se", "s2", "energy"):
+        assert np.allclose(merged[k], g[k], rtol=1e-9, atol=1e-12), k
+    p.close()
