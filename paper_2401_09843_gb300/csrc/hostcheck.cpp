@@ -91,7 +91,7 @@ template <typename T, int N1, int N2>
 void run_zfast(const ZArgs<T>& a, int nm) {
   using S = ZFastShape<N1, N2>;
   std::vector<cplx<T>> sm(S::SM_ELEMS);
-  std::vector<double> red(S::NTHR);
+  std::vector<T> red(S::NTHR);
   std::vector<ZFastState<T, N1, N2>> st(S::NTHR);
   const int gx = (S::P + S::Y - 1) / S::Y;
   for (int bz = 0; bz < nm; ++bz)
@@ -102,7 +102,7 @@ void run_zfast(const ZArgs<T>& a, int nm) {
         for (int t = 0; t < S::NTHR; ++t) zfast_inv1(c, t, S::NTHR);
         for (int t = 0; t < S::NTHR; ++t) {
           zfast_inv2(c, t, st[t]);
-          red[t] = st[t].bad ? -1.0 : (double)st[t].umax;
+          red[t] = st[t].bad ? T(-1) : st[t].umax;
         }
         zfast_reduce(c, red.data(), S::NTHR);
         for (int r = 0; r < 2; ++r) {

@@ -11,7 +11,7 @@ __global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, 2) k_zfast(ZArgs<T> 
   using S = ZFastShape<N1, N2>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
-  double* red = reinterpret_cast<double*>(sm + S::SM_ELEMS);
+  T* red = reinterpret_cast<T*>(sm + S::SM_ELEMS);
   const ZFastCtx<T, N1, N2> c = zfast_ctx<T, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
   const int tid = threadIdx.x;
   zfast_load_twiddles(c, tid, S::NTHR);
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, 2) k_zfast(ZArgs<T> 
   __syncthreads();
   ZFastState<T, N1, N2> st;
   zfast_inv2(c, tid, st);
-  red[tid] = st.bad ? -1.0 : (double)st.umax;
+  red[tid] = st.bad ? T(-1) : st.umax;
   __syncthreads();
   if (tid == 0) zfast_reduce(c, red, S::NTHR);
 #pragma unroll

@@ -272,16 +272,18 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
       if (!(s <= big_finite<T>())) bad = 1;
       else m = s > m ? s : m;
     }
-    red[tid] = bad ? -1.0 : (double)m;
+    T* tred = reinterpret_cast<T*>(red);
+    tred[tid] = bad ? T(-1) : m;
     sync();
     if (tid == 0) {
-      double mm = 0.0;
+      T mm = T(0);
       int anybad = 0;
       for (int i = 0; i < nthr; ++i) {
-        if (red[i] < 0) anybad = 1;
-        else if (red[i] > mm) mm = red[i];
+        const T r = tred[i];
+        anybad |= r < T(0);
+        mm = r > mm ? r : mm;
       }
-      atomic_max_u64(&a.ctrl[bz].umax_bits, dbl_bits(mm));
+      atomic_max_u64(&a.ctrl[bz].umax_bits, dbl_bits((double)mm));
       if (anybad) atomic_or_i32(&a.ctrl[bz].status, NS3D_FLAG_NONFINITE);
     }
   }

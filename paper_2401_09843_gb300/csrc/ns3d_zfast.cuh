@@ -49,6 +49,7 @@ struct ZFastShape {
   // (stride N1 + 1 or N2 + 1 across threads) hit distinct shared-memory banks.
   static constexpr int LP = P + (N1 > N2 ? N1 : N2);
   // shared memory in complex elements: two twiddle tables + exchange [NPAIR][3][LP]
+  // (followed by NTHR reduction slots of T)
   static constexpr int SM_ELEMS = 2 * P + NPAIR * 3 * LP;
 };
 
@@ -112,11 +113,27 @@ NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     const cplx<T>* ia = in + (l == 2 ? 2 : 0) * a.in_cs;
     const cplx<T>* ib = in + (l == 2 ? 2 : 1) * a.in_cs;
     cplx<T> v[N1];
+    const bool full = (S::P % S::Y == 0);     // every tile has Y columns
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       // positions N2 j1 .. N2 j1 + N2 - 1: the zero band is known at compile time
-      if (pad_region(N2 * j1, N2, S::P, S::H) == PAD_ZERO) v[j1] = czero<T>();
-      else v[j1] = pack2(ia, ib, S::P, S::H, N2 * j1 + j2, ca, cb, c.ncol);
+      const int p = N2 * j1 + j2;
+      const int reg = pad_region(N2 * j1, N2, S::P, S::H);
+      if (reg == PAD_ZERO) {
+        v[j1] = czero<T>();
+      } else if (full && reg == PAD_LOW) {          // u_a[p] + i u_b[p]
+        cplx<T> x = ia[ca * h + p], y = ib[cb * h + p];
+        if (j1 == 0 && p == 0) {
+          x.y = T(0);
+          y.y = T(0);
+        }
+        v[j1] = cmake(x.x - y.y, x.y + y.x);
+      } else if (full && reg == PAD_HIGH) {         // conj(u_a[P-p]) + i conj(u_b[P-p])
+        const cplx<T> x = ia[ca * h + (S::P - p)], y = ib[cb * h + (S::P - p)];
+        v[j1] = cmake(x.x + y.y, -x.y + y.x);
+      } else {
+        v[j1] = pack2(ia, ib, S::P, S::H, p, ca, cb, c.ncol);
+      }
     }
     Dft<N1, +1>::run(v);
     cplx<T>* X = c.X + (g * 3 + l) * S::LP;
@@ -232,16 +249,19 @@ NS3D_HD void zfast_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr, int 
   }
 }
 
+// Block maximum of the per-thread maxima (in T: FP64 instructions are slow on
+// this part), one atomic per block; a negative entry flags a non-finite value.
 template <typename T, int N1, int N2>
-NS3D_HD void zfast_reduce(const ZFastCtx<T, N1, N2>& c, const double* red, int nthr) {
+NS3D_HD void zfast_reduce(const ZFastCtx<T, N1, N2>& c, const T* red, int nthr) {
   const ZArgs<T>& a = *c.a;
   if (!a.ctrl) return;
-  double m = 0.0;
+  T m = T(0);
   int bad = 0;
   for (int i = 0; i < nthr; ++i) {
-    if (red[i] < 0) bad = 1;
-    else if (red[i] > m) m = red[i];
+    const T r = red[i];
+    bad |= r < T(0);
+    m = r > m ? r : m;
   }
-  atomic_max_u64(&a.ctrl[c.bz].umax_bits, dbl_bits(m));
+  atomic_max_u64(&a.ctrl[c.bz].umax_bits, dbl_bits((double)m));
   if (bad) atomic_or_i32(&a.ctrl[c.bz].status, NS3D_FLAG_NONFINITE);
 }
