@@ -36,6 +36,68 @@ METRIC = "grid-pt-steps/s at 256^3 (plain vs batched FP32 ensemble), % of HBM ro
 UNIT = "grid-pt-steps/s"
 
 
+ENSEMBLE_LEVELS = [(64, 256, 1000), (128, 32, 2000), (256, 4, 3000)]   # (N, members, seed base)
+
+
+def _ic(args):
+    N, seed, member = args
+    import ns3d_inputs as I
+    return I.random_spectrum(N, seed=seed, member=member)
+
+
+def ensemble_ics(levels):
+    """Seeded initial data of every member, built in a spawn-started pool."""
+    import multiprocessing as mp
+    jobs = [(N, base, m) for N, M, base in levels for m in range(M)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        return pool.map(_ic, jobs, chunksize=4)
+
+
+def bench_ensemble(B, torch, steps: int, warmup: int, to_t: float = 0.0):
+    """Batched uneven FP32 ensemble: 256 x 64^3 + 32 x 128^3 + 4 x 256^3 members
+    in one plan (one level per resolution), per-member CFL steps."""
+    Ns = [N for N, M, _ in ENSEMBLE_LEVELS for _ in range(M)]
+    ics = ensemble_ics(ENSEMBLE_LEVELS)
+    plan = B.Plan(Ns, B.NS3D_F32, eps0=1.0, cfl=0.5)
+    for m, u in enumerate(ics):
+        plan.set_initial(m, u)
+    del ics
+    stream = torch.cuda.current_stream()
+    plan.step(warmup, t_end=to_t)
+    plan.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.step(steps, t_end=to_t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pts = sum(N ** 3 for N in Ns)
+    info = {"members": {str(N): M for N, M, _ in ENSEMBLE_LEVELS}, "steps": steps,
+            "ms_per_step": ms / steps, "value": pts * steps / (ms * 1e-3), "unit": UNIT,
+            "samples_steps_per_s": len(Ns) * steps / (ms * 1e-3),
+            "gpu_launches_per_step": plan.info(0)["launches_per_step"]}
+    plan.close()
+    return info
+
+
+def bench_plain_fp64(B, torch, N: int, steps: int):
+    import ns3d_inputs as I
+    plan = B.Plan([N], B.NS3D_F64, eps0=1.0, cfl=0.5)
+    plan.set_initial(0, I.random_spectrum(N, seed=20240001))
+    plan.step(1)
+    plan.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    plan.close()
+    return {"N": N, "steps": steps, "ms_per_step": ms / steps,
+            "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -47,6 +109,8 @@ def parse():
     ap.add_argument("--members", type=int, default=1, help="members per GPU at N")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-ensemble and FP64 comparison lines")
     return ap.parse_args()
 
 
@@ -337,6 +401,9 @@ def main():
         "e2e": e2e,
         "status_ok": status_ok,
     }
+    if not args.no_extras and world == 1:
+        line["batched_ensemble"] = bench_ensemble(B, torch, steps=10, warmup=2)
+        line["plain_fp64"] = bench_plain_fp64(B, torch, N, steps=3)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
