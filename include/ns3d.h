@@ -189,10 +189,13 @@ ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);
 /* Diagnostic: advances every member by `nsteps` steps like ns3d_step, but
  * launches the kernels one by one (no graph) with CUDA events recorded on the
  * plan's stream around each of them, and adds the measured milliseconds of
- * each kernel kind to kernel_ms[0..5] and the number of launches to
+ * each kernel kind to kernel_ms[0..5] and the number of stage evaluations to
  * launches[0..5] (kinds: 0 inverse x, 1 inverse y, 2 fused z pass, 3 forward
- * y, 4 forward x, 5 spectral step).  Synchronises.  The paper times single
- * kernel calls the same way to compare them with lower bounds (Table 2). */
+ * y, 4 forward x, 5 spectral step; where a level runs the fused x pass -- the
+ * forward x, spectral step and next stage's inverse x in one kernel -- its
+ * time is under kind 5 and kinds 0 and 4 stay at zero).  Synchronises.  The
+ * paper times single kernel calls the same way to compare them with lower
+ * bounds (Table 2). */
 ns3d_status ns3d_step_timed(ns3d_plan plan, int nsteps, double t_end, double* kernel_ms,
                             int* launches);
 

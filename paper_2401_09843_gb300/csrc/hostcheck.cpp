@@ -6,11 +6,13 @@
 // API: the library itself never runs on the host.
 #include <algorithm>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "ns3d_geom.h"
 #include "ns3d_zfast.cuh"
 #include "ns3d_colfast.cuh"
+#include "ns3d_xfused.cuh"
 
 namespace {
 
@@ -126,6 +128,107 @@ bool run_z_fast_if_any(const ZArgs<T>& a, int P) {
   return false;
 }
 
+// The fused x pass, phase by phase and thread by thread, on member 0.  The
+// staging ring is filled at the same points as the kernel's tile loads (a
+// copy lands at once), after the slots were poisoned with NaN, so a phase
+// that read a slot before its tile or after its reuse shows in the result.
+template <typename T, int N1, int N2>
+void run_xfused(const XFusedArgs<T>& a) {
+  using S = XFusedShape<N1, N2>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  cplx<T>* ring = sm.data();
+  cplx<T>* tw = ring + S::OFF_TW;
+  cplx<T>* X = ring + S::OFF_X;
+  std::vector<XFusedState<T, N1, N2>> st(S::NTHR);
+  std::vector<cplx<T>> v((size_t)S::NTHR * N2);
+  const int ncols = a.N * a.h;
+  const int L = xf_num_tiles(a.stage);
+  const T nan = std::numeric_limits<T>::quiet_NaN();
+  for (int bx = 0; bx < ncols / S::W; ++bx) {
+    auto issue = [&](int j) {
+      if (j >= L) return;
+      const XfTile t = xf_tile<N1, N2>(j, 0, a.stage);
+      const cplx<T>* src = t.src == 0 ? a.dq : (t.src == 1 ? a.u0 : a.us);
+      cplx<T>* dst = ring + (j % S::NSLOT) * S::SLOT;
+      for (int r = 0; r < S::H; ++r)
+        for (int c = 0; c < S::W; ++c) dst[r * S::W + c] = src[(t.row + r) * ncols + bx * S::W + c];
+    };
+    for (int e = 0; e < S::SM_ELEMS; ++e) sm[e] = cmake(nan, nan);
+    for (int j = 0; j < S::NSLOT; ++j) issue(j);
+    for (int t = 0; t < S::NTHR; ++t) xfused_twiddles<T, N1, N2>(a, tw, t, S::NTHR);
+    for (auto& x : st)
+      for (int q = 0; q < 3; ++q)
+        for (int k = 0; k < N2; ++k) x.v[q][k] = czero<T>();
+    for (int q = 0; q < 6; ++q) {
+      for (int t = 0; t < S::NTHR; ++t) xfused_fwd1<T, N1, N2>(q, t, S::NTHR, ring, tw, X);
+      for (int j = 3 * q; j < 3 * q + 3; ++j) issue(j + S::NSLOT);
+      for (int t = 0; t < S::NTHR; ++t) xfused_fwd2<T, N1, N2>(a, bx, q, t, X, st[t]);
+    }
+    for (int t = 0; t < S::NTHR; ++t) xfused_leray<T, N1, N2>(a, bx, t, st[t]);
+    for (int q = 0; q < 3; ++q) {
+      const int cl = xf_comp_tiles(a.stage), j0 = 18 + q * cl;
+      for (int t = 0; t < S::NTHR; ++t) {
+        xfused_combine<T, N1, N2>(a, bx, 0, q, t, ring, st[t], &v[(size_t)t * N2]);
+        xfused_inv1<T, N1, N2>(t, tw, X, &v[(size_t)t * N2]);
+      }
+      for (int j = j0; j < j0 + cl; ++j) issue(j + S::NSLOT);
+      for (int t = 0; t < S::NTHR; ++t) xfused_inv2<T, N1, N2>(a, bx, 0, q, t, S::NTHR, X);
+    }
+    for (int t = 0; t < S::NTHR; ++t) xfused_clock<T, N1, N2>(a, bx, 0, t);
+  }
+}
+
+template <typename T>
+bool fused_shape(const ns3d::Geom& g) {
+  if (!g_use_fast || sizeof(T) != 4 || 3 * g.h != g.P) return false;
+#define NS3D_HC_XS(A, B) \
+  if (g.P == (A) * (B)) return true;
+  NS3D_FOR_XFUSED(NS3D_HC_XS)
+#undef NS3D_HC_XS
+  return false;
+}
+
+// One stage with the fused x pass (W1 holds the x-inverse of `in` on entry,
+// and of `out` on exit).
+template <typename T>
+void fused_stage(const ns3d::Geom& g, const SpecParams& sp, cplx<T>* u0, cplx<T>* us,
+                 cplx<T>* out, int stage, std::vector<cplx<T>>& W1, std::vector<cplx<T>>& W2,
+                 const std::vector<cplx<T>>& tw, Ns3dCtrl* ctrl, std::vector<cplx<T>>& sm) {
+  using namespace ns3d;
+  run_col<T, +1, true, true>(args_inv_y<T>(g, W1.data(), W2.data(), tw.data()), launch_inv_y(g, 1), sm);
+  {
+    ZArgs<T> za = args_z<T>(g, W2.data(), W1.data(), tw.data(), stage == 1 ? ctrl : nullptr);
+    if (!run_z_fast_if_any<T>(za, g.P)) run_z<T>(za, launch_z(g, 1), sm);
+  }
+  run_col<T, -1, true, true>(args_fwd_y<T>(g, W1.data(), W2.data(), tw.data()), launch_fwd_y(g, 1), sm);
+  if (stage == 1) step_dt_member(*ctrl, sp);
+  XFusedArgs<T> x{};
+  x.dq = W2.data();
+  x.u0 = u0;
+  x.us = us;
+  x.out = out;
+  x.ax = W1.data();
+  x.tw = tw.data();
+  std::vector<T> lam(3 * (g.h - 1) * (g.h - 1) + 1);
+  {
+    const SpecT<double> spd = spec_t<double>(sp);
+    for (size_t k2 = 0; k2 < lam.size(); ++k2) lam[k2] = T(lambda_k<double>((int)k2, spd));
+  }
+  x.lam = lam.data();
+  x.N = g.N;
+  x.h = g.h;
+  x.stage = stage;
+  x.m6 = g.nDq;
+  x.m3 = g.nU;
+  x.mA = g.nA;
+  x.sp = spec_t<T>(sp);
+  x.ctrl = ctrl;
+#define NS3D_HC_XF(A, B) \
+  if (g.P == (A) * (B)) run_xfused<T, A, B>(x);
+  NS3D_FOR_XFUSED(NS3D_HC_XF)
+#undef NS3D_HC_XF
+}
+
 // One evaluation of Algorithm 2 and the spectral step on member 0.
 template <typename T>
 void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cplx<T>* u0,
@@ -178,10 +281,20 @@ int run(int N, int P, const double* prm, const void* uin, void* uout, int nsteps
     compact_to_d1(US.data(), (cplx<T>*)uout, N);
     return 0;
   }
-  for (int n = 0; n < nsteps; ++n) {
-    rhs_stage<T>(g, sp, U0.data(), U0.data(), US.data(), US.data(), 1, W1, W2, tw, &ctrl, sm);
-    rhs_stage<T>(g, sp, US.data(), U0.data(), US.data(), US.data(), 2, W1, W2, tw, &ctrl, sm);
-    rhs_stage<T>(g, sp, US.data(), U0.data(), US.data(), U0.data(), 3, W1, W2, tw, &ctrl, sm);
+  if (fused_shape<T>(g)) {
+    run_col<T, +1, true, true>(ns3d::args_inv_x<T>(g, U0.data(), W1.data(), tw.data()),
+                               ns3d::launch_inv_x(g, 1), sm);
+    for (int n = 0; n < nsteps; ++n) {
+      fused_stage<T>(g, sp, U0.data(), US.data(), US.data(), 1, W1, W2, tw, &ctrl, sm);
+      fused_stage<T>(g, sp, U0.data(), US.data(), US.data(), 2, W1, W2, tw, &ctrl, sm);
+      fused_stage<T>(g, sp, U0.data(), US.data(), U0.data(), 3, W1, W2, tw, &ctrl, sm);
+    }
+  } else {
+    for (int n = 0; n < nsteps; ++n) {
+      rhs_stage<T>(g, sp, U0.data(), U0.data(), US.data(), US.data(), 1, W1, W2, tw, &ctrl, sm);
+      rhs_stage<T>(g, sp, US.data(), U0.data(), US.data(), US.data(), 2, W1, W2, tw, &ctrl, sm);
+      rhs_stage<T>(g, sp, US.data(), U0.data(), US.data(), U0.data(), 3, W1, W2, tw, &ctrl, sm);
+    }
   }
   compact_to_d1(U0.data(), (cplx<T>*)uout, N);
   if (t_out) *t_out = ctrl.t;

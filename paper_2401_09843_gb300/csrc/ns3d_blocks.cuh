@@ -43,6 +43,7 @@ struct Ns3dCtrl {
 
 #define NS3D_FLAG_NONFINITE 1
 #define NS3D_FLAG_UNSTABLE 2
+#define NS3D_FLAG_TIMEOUT 4   // a staged copy did not arrive within its time limit
 
 NS3D_HD void atomic_max_u64(unsigned long long* p, unsigned long long v) {
 #if defined(__CUDA_ARCH__)

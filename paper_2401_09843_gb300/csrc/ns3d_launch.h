@@ -3,11 +3,13 @@
 // them in parallel; this header only declares them.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ns3d_geom.h"
 #include "ns3d_zfast.cuh"
 #include "ns3d_colfast.cuh"
+#include "ns3d_xfused.cuh"
 
 namespace ns3d {
 
@@ -48,6 +50,44 @@ cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaS
     case COL_INV_CC: return col_launch<T, +1, true, true>(a, L, s);
     case COL_FWD_CC: return col_launch<T, -1, true, true>(a, L, s);
   }
+  return cudaErrorInvalidValue;
+}
+
+// TMA descriptors of the fused x pass's inputs (each array of a level viewed
+// as FP32 [rows][2 N h], boxes of N/2 rows x 16 complex columns)
+struct XFusedMaps {
+  CUtensorMap dq, u0, us;
+};
+
+// encodes the maps for a level of B members (xfused_maps.cu); false if the
+// driver refuses them
+bool xfused_make_maps(XFusedMaps* maps, const Geom& g, int B, const void* dq, const void* u0,
+                      const void* us);
+
+template <typename T, int N1, int N2>
+cudaError_t xfused_launch(const XFusedArgs<T>& a, const XFusedMaps& maps, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t xfused_init();
+
+// The fused x pass exists for FP32 at P = N1 N2 with the default padding.
+template <typename T>
+bool xfused_available(const Geom& g) {
+  if (sizeof(T) != 4 || 3 * g.h != g.P || (g.N * g.h) % 16 != 0) return false;
+#define NS3D_XF_CASE(A, B) \
+  if (g.P == (A) * (B)) return true;
+  NS3D_FOR_XFUSED(NS3D_XF_CASE)
+#undef NS3D_XF_CASE
+  return false;
+}
+
+template <typename T>
+cudaError_t launch_xfused(const XFusedArgs<T>& a, const XFusedMaps& maps, const Geom& g, int nm,
+                          cudaStream_t s) {
+  const XFusedArgs<float>& af = *reinterpret_cast<const XFusedArgs<float>*>(&a);
+#define NS3D_XF_GO(A, B) \
+  if (g.P == (A) * (B)) return xfused_launch<float, A, B>(af, maps, nm, s);
+  NS3D_FOR_XFUSED(NS3D_XF_GO)
+#undef NS3D_XF_GO
   return cudaErrorInvalidValue;
 }
 
@@ -98,6 +138,13 @@ cudaError_t kernels_init() {
     }
     NS3D_FOR_ZFAST(NS3D_ZF_INIT)
 #undef NS3D_ZF_INIT
+#define NS3D_XF_INIT(A, B)                                  \
+    {                                                       \
+      cudaError_t r = xfused_init<float, A, B>();           \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_XFUSED(NS3D_XF_INIT)
+#undef NS3D_XF_INIT
 #define NS3D_CF_INIT(A, B)                                                         \
     {                                                                              \
       cudaError_t r1 = colfast_init<float, +1, A, B>();                            \

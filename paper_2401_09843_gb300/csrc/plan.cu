@@ -35,6 +35,10 @@ struct Level {
   void* W2 = nullptr;
   void* twP = nullptr;
   Ns3dCtrl* ctrl = nullptr;
+  bool fused = false;     // the step uses the fused x pass (FP32 register sizes)
+  bool a_valid = false;   // W1 holds the x-inverse of U0 (set by the last step)
+  XFusedMaps maps{};      // TMA descriptors of W2 (Dq), U0, US for the fused x pass
+  void* lamT = nullptr;   // lambda_k by |k|^2 (fused levels)
 };
 
 struct DeviceGuard {
@@ -138,6 +142,21 @@ ns3d_status upload_twiddles(Level& L, cudaStream_t s) {
   return NS3D_OK;
 }
 
+// lambda_k by integer |k|^2 over the retained band (0 .. 3 (h - 1)^2),
+// evaluated in double and rounded once to the arithmetic type
+template <typename T>
+ns3d_status upload_lambda(Level& L, cudaStream_t s) {
+  const int hm = L.g.h - 1;
+  const SpecT<double> sp = spec_t<double>(L.sp);
+  std::vector<T> lam(3 * hm * hm + 1);
+  for (size_t k2 = 0; k2 < lam.size(); ++k2) lam[k2] = T(lambda_k<double>((int)k2, sp));
+  NS3D_CK(cudaMemcpyAsync(L.lamT, lam.data(), lam.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  NS3D_CK(cudaStreamSynchronize(s));
+  return NS3D_OK;
+}
+
+size_t lambda_entries(const Geom& g) { return 3 * (size_t)(g.h - 1) * (g.h - 1) + 1; }
+
 // One evaluation of Algorithm 2 plus the spectral step for members
 // [m0, m0 + nm) of a level.  `in` is the field R is evaluated at; stage 0
 // writes R to `out`, stages 1-3 the SSP-RK3 combinations.
@@ -154,13 +173,40 @@ StageBufs level_bufs(Level& L, int m0) {
   b.u0 = static_cast<unsigned char*>(L.U0) + (size_t)m0 * L.g.nU * L.g.esz;
   b.us = static_cast<unsigned char*>(L.US) + (size_t)m0 * L.g.nU * L.g.esz;
   b.ctrl = L.ctrl + m0;
+  b.fused = false;
   return b;
 }
 
 template <typename T>
 ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in, cplx<T>* out,
                           bool want_umax, cudaStream_t s, KernelTimer* tm = nullptr) {
-  return enqueue_rhs<T>(level_bufs(L, m0), stage, nm, in, out, want_umax, s, tm);
+  StageBufs b = level_bufs(L, m0);
+  b.fused = L.fused && stage >= 1 && m0 == 0 && nm == L.B;
+  b.maps = &L.maps;
+  b.lam = L.lamT;
+  return enqueue_rhs<T>(b, stage, nm, in, out, want_umax, s, tm);
+}
+
+// x-inverse of every member's state into W1 (needed before the first fused
+// stage after the state or W1 changed outside a step)
+template <typename T>
+ns3d_status enqueue_prologue(Level& L, cudaStream_t s) {
+  const cplx<T>* U0 = static_cast<const cplx<T>*>(L.U0);
+  NS3D_CK(launch_col<T>(args_inv_x<T>(L.g, U0, static_cast<cplx<T>*>(L.W1),
+                                      static_cast<const cplx<T>*>(L.twP)),
+                        COL_INV_CC, launch_inv_x(L.g, L.B), s));
+  L.a_valid = true;
+  return NS3D_OK;
+}
+
+ns3d_status ensure_prologue(ns3d_plan p) {
+  for (Level& L : p->levels) {
+    if (!L.fused || L.a_valid) continue;
+    ns3d_status st = p->dtype == NS3D_F32 ? enqueue_prologue<float>(L, p->stream)
+                                          : enqueue_prologue<double>(L, p->stream);
+    if (st != NS3D_OK) return st;
+  }
+  return NS3D_OK;
 }
 
 }  // namespace
@@ -178,7 +224,8 @@ ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in
   cplx<T>* U0 = static_cast<cplx<T>*>(b.u0);
   cplx<T>* US = static_cast<cplx<T>*>(b.us);
   NS3D_MARK(0);
-  NS3D_CK(launch_col<T>(args_inv_x<T>(g, in, W1, tw), COL_INV_CC, launch_inv_x(g, nm), s));
+  if (!b.fused)
+    NS3D_CK(launch_col<T>(args_inv_x<T>(g, in, W1, tw), COL_INV_CC, launch_inv_x(g, nm), s));
   NS3D_MARK(1);
   NS3D_CK(launch_col<T>(args_inv_y<T>(g, W1, W2, tw), COL_INV_CC, launch_inv_y(g, nm), s));
   NS3D_MARK(2);
@@ -186,6 +233,30 @@ ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in
   NS3D_MARK(3);
   NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W1, W2, tw), COL_FWD_CC, launch_fwd_y(g, nm), s));
   NS3D_MARK(4);
+  if (b.fused) {
+    // forward x + spectral step + RK3 combine + inverse x of the new state
+    XFusedArgs<T> x{};
+    x.dq = W2;
+    x.u0 = U0;
+    x.us = US;
+    x.out = out;
+    x.ax = W1;
+    x.tw = tw;
+    x.lam = static_cast<const T*>(b.lam);
+    x.N = g.N;
+    x.h = g.h;
+    x.stage = stage;
+    x.m6 = g.nDq;
+    x.m3 = g.nU;
+    x.mA = g.nA;
+    x.sp = spec_t<T>(b.sp);
+    x.ctrl = b.ctrl;
+    NS3D_MARK(5);
+    if (stage == 1) NS3D_CK(launch_step_dt(b.ctrl, nm, b.sp, s));
+    NS3D_CK(launch_xfused<T>(x, *b.maps, g, nm, s));
+    NS3D_MARK(6);
+    return NS3D_OK;
+  }
   NS3D_CK(launch_col<T>(args_fwd_x<T>(g, W2, W1, tw), COL_FWD_CC, launch_fwd_x(g, nm), s));
   NS3D_MARK(5);
   SpecArgs<T> a{};
@@ -280,6 +351,7 @@ ns3d_status get_d1(ns3d_plan p, Level& L, const cplx<T>* src, void* dst, int on_
 ns3d_status status_of_flags(int flags) {
   if (flags & NS3D_FLAG_NONFINITE) return NS3D_ERR_NONFINITE;
   if (flags & NS3D_FLAG_UNSTABLE) return NS3D_ERR_UNSTABLE_DT;
+  if (flags & NS3D_FLAG_TIMEOUT) return NS3D_ERR_TIMEOUT;
   return NS3D_OK;
 }
 
@@ -328,6 +400,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     if (!make_geom(L.N, L.P, p->esz, &L.g)) { delete p; return NS3D_ERR_NOT_SUPPORTED; }
     L.sp = make_spec_params(L.N, L.P, P.L, P.nu, P.s, P.theta, P.eps0, P.mN_coef, P.q_form, P.cfl,
                             P.dt_fixed);
+    L.fused = dtype == NS3D_F32 ? xfused_available<float>(L.g) : xfused_available<double>(L.g);
     const Geom& g = L.g;
     need += (size_t)L.B * (2 * g.nU + g.nW1 + g.nW2) * p->esz + (size_t)L.P * p->esz +
             (size_t)L.B * sizeof(Ns3dCtrl);
@@ -364,6 +437,12 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     L.ctrl = static_cast<Ns3dCtrl*>(c);
     st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
     if (st != NS3D_OK) break;
+    if (L.fused && !xfused_make_maps(&L.maps, g, L.B, L.W2, L.U0, L.US)) L.fused = false;
+    if (L.fused) {
+      if ((st = dev_alloc(p, &L.lamT, lambda_entries(g) * sizeof(float))) != NS3D_OK) break;
+      st = upload_lambda<float>(L, p->stream);
+      if (st != NS3D_OK) break;
+    }
     if (cudaMemsetAsync(L.U0, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
         cudaMemsetAsync(L.US, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
         launch_ctrl_reset(L.ctrl, L.B, p->stream) != cudaSuccess)
@@ -377,7 +456,8 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     return st;
   }
   p->staging_bytes = stag;
-  p->launches_per_step = 19 * (int)p->levels.size();
+  p->launches_per_step = 0;
+  for (const Level& L : p->levels) p->launches_per_step += L.fused ? 13 : 19;
   *out = p;
   return NS3D_OK;
 }
@@ -418,6 +498,7 @@ extern "C" ns3d_status ns3d_set_initial(ns3d_plan p, int member, const void* uha
   if (st != NS3D_OK) return st;
   NS3D_CK(launch_ctrl_reset(L->ctrl + idx, 1, p->stream));
   NS3D_CK(launch_ctrl_set_tend(L->ctrl + idx, 1, p->t_end, p->stream));
+  L->a_valid = false;
   if (!on_device) NS3D_CK(cudaStreamSynchronize(p->stream));
   return NS3D_OK;
 }
@@ -450,7 +531,9 @@ extern "C" ns3d_status ns3d_step(ns3d_plan p, int nsteps, double t_end) {
     for (Level& L : p->levels) NS3D_CK(launch_ctrl_set_tend(L.ctrl, L.B, t_end, p->stream));
     p->t_end = t_end;
   }
-  ns3d_status st = build_graph(p);
+  ns3d_status st = ensure_prologue(p);
+  if (st != NS3D_OK) return st;
+  st = build_graph(p);
   if (st != NS3D_OK) return st;
   for (int i = 0; i < nsteps; ++i) NS3D_CK(cudaGraphLaunch(p->exec, p->stream));
   return NS3D_OK;
@@ -488,6 +571,7 @@ extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, 
     if ((st = enqueue_stage<double>(*L, 0, idx, 1, slot, slot, false, p->stream)) != NS3D_OK) return st;
     if ((st = get_d1<double>(p, *L, slot, rhs, on_device)) != NS3D_OK) return st;
   }
+  L->a_valid = false;   // the evaluation used W1
   if (!on_device) NS3D_CK(cudaStreamSynchronize(p->stream));
   return NS3D_OK;
 }
@@ -500,9 +584,10 @@ extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, do
     for (Level& L : p->levels) NS3D_CK(launch_ctrl_set_tend(L.ctrl, L.B, t_end, p->stream));
     p->t_end = t_end;
   }
+  ns3d_status st = ensure_prologue(p);
+  if (st != NS3D_OK) return st;
   KernelTimer tm;
   for (int i = 0; i < 7; ++i) NS3D_CK(cudaEventCreate(&tm.ev[i]));
-  ns3d_status st = NS3D_OK;
   for (int n = 0; n < nsteps && st == NS3D_OK; ++n) {
     for (Level& L : p->levels) {
       for (int stage = 1; stage <= 3 && st == NS3D_OK; ++stage) {
@@ -524,6 +609,7 @@ extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, do
           break;
         }
         for (int k = 0; k < 6; ++k) {
+          if (L.fused && (k == 0 || k == 4)) continue;   // folded into kind 5
           float ms = 0.f;
           if (cudaEventElapsedTime(&ms, tm.ev[k], tm.ev[k + 1]) != cudaSuccess) {
             st = NS3D_ERR_CUDA;

@@ -7,6 +7,10 @@
 #include "ns3d.h"
 #include "ns3d_geom.h"
 
+namespace ns3d {
+struct XFusedMaps;
+}
+
 struct LevelView {
   int N = 0, P = 0, B = 0;
   int index = 0;                 // level number in the plan
@@ -39,6 +43,11 @@ struct StageBufs {
   void* u0 = nullptr;         // state at t_n
   void* us = nullptr;         // stage state
   Ns3dCtrl* ctrl = nullptr;   // per member (dt; CFL maximum when wanted)
+  // stages 1-3 with the fused x pass: W1 already holds the x-inverse (A) of
+  // `in`, and the stage leaves A of `out` in W1 (no separate inverse x)
+  bool fused = false;
+  const ns3d::XFusedMaps* maps = nullptr;   // TMA descriptors (fused stages)
+  const void* lam = nullptr;                 // lambda_k by |k|^2 (fused stages)
 };
 
 // Optional per-kernel timing: events recorded before each kernel kind.

@@ -157,3 +157,42 @@ def test_emulated_register_kernels_match_oracle(built, N, P):
     finally:
         lib.ns3d_hostcheck_use_fast(1)
     assert rel(gen32, ref) < 2e-6
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_emulated_fused_x_steps_match_oracle(built, N):
+    """Steps with the fused x pass (forward x + spectral + RK3 + next inverse x
+    in one kernel; FP32, P = 3N/2), emulated thread by thread, against the
+    oracle and against the unfused emulated kernels; CFL steps."""
+    prm = S.Params(nu=0.005, eps0=1.0)
+    uh = I.random_spectrum(N, seed=N + 1, k0=3.0)
+    ref, tref, _ = S.integrate(uh, prm, 2)
+    got, rc, t = hostcheck(built, uh, 3 * N // 2, prm, nsteps=2, dtype=0)
+    assert rc == 0 and abs(t - tref) < 1e-6 * tref
+    assert rel(got, ref) < 2e-5
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_use_fast(0)
+    try:
+        gen, _, tg = hostcheck(built, uh, 3 * N // 2, prm, nsteps=2, dtype=0)
+    finally:
+        lib.ns3d_hostcheck_use_fast(1)
+    assert rel(got, gen) < 2e-6
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_emulated_fused_x_large_tiles(built, N):
+    """The fused x pass at P = 192 and 384 (radix 12 x 16 and 24 x 16),
+    emulated thread by thread: one fixed-dt step of a sparse field against the
+    unfused emulated kernels."""
+    prm = S.Params(nu=0.01, eps0=1.0)
+    uh = I.sparse_random(N, seed=N + 7, nmodes=24)
+    got, rc, _ = hostcheck(built, uh, 3 * N // 2, prm, nsteps=1, dt=1e-3, dtype=0)
+    assert rc == 0
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_use_fast(0)
+    try:
+        gen, _, _ = hostcheck(built, uh, 3 * N // 2, prm, nsteps=1, dt=1e-3, dtype=0)
+    finally:
+        lib.ns3d_hostcheck_use_fast(1)
+    assert rel(got, gen) < 2e-6
+    assert rel(got, uh) > 1e-6     # the step changed the field
