@@ -106,11 +106,11 @@ void run_zfast(const ZArgs<T>& a, int nm) {
           zfast_inv2(c, t, st[t]);
           red[t] = st[t].bad ? T(-1) : st[t].umax;
         }
-        zfast_reduce(c, red.data(), S::NTHR);
+        zfast_reduce(c, red.data(), S::NTHR, 0);
         for (int r = 0; r < 2; ++r) {
           for (int t = 0; t < S::NTHR; ++t) zfast_fwd1(c, t, st[t], r);
           for (int t = 0; t < S::NTHR; ++t) zfast_fwd2(c, t, S::NTHR);
-          for (int t = 0; t < S::NTHR; ++t) zfast_extract(c, t, S::NTHR, r);
+          for (int t = 0; t < S::NTHR; ++t) zfast_extract(c, t, r);
         }
       }
 }

@@ -22,14 +22,14 @@ __global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, 2) k_zfast(ZArgs<T> 
   zfast_inv2(c, tid, st);
   red[tid] = st.bad ? T(-1) : st.umax;
   __syncthreads();
-  if (tid == 0) zfast_reduce(c, red, S::NTHR);
+  if (tid < 32) zfast_reduce(c, red, S::NTHR, tid);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     zfast_fwd1(c, tid, st, r);
     __syncthreads();
     zfast_fwd2(c, tid, S::NTHR);
     __syncthreads();
-    zfast_extract(c, tid, S::NTHR, r);
+    zfast_extract(c, tid, r);
     __syncthreads();
   }
 }

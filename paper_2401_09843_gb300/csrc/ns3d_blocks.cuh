@@ -27,6 +27,9 @@ template <> NS3D_HD double big_finite<double>() { return 1.7976931348623157e308;
 NS3D_HD float xabs(float a) { return fabsf(a); }
 NS3D_HD double xabs(double a) { return fabs(a); }
 NS3D_HD float xpow(float a, float b) { return powf(a, b); }
+// maximum that ignores a NaN operand
+NS3D_HD float xmax(float a, float b) { return fmaxf(a, b); }
+NS3D_HD double xmax(double a, double b) { return fmax(a, b); }
 NS3D_HD double xpow(double a, double b) { return pow(a, b); }
 
 // Per-member control word kept in device memory.

@@ -139,7 +139,7 @@ NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     cplx<T>* X = c.X + (g * 3 + l) * S::LP;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      X[j2 * (N1 + 1) + k1] = (k1 == 0 || j2 == 0) ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];
+      X[j2 * (N1 + 1) + k1] = k1 == 0 ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];   // twi[k1 N2] = 1
   }
 }
 
@@ -158,20 +158,26 @@ NS3D_HD void zfast_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZFastState<T, N1,
     for (int j = 0; j < N2; ++j) st.z[l][j] = X[j * (N1 + 1) + k1];
     Dft<N2, +1>::run(st.z[l]);
   }
-  const bool va = 2 * g < c.ncol, vb = 2 * g + 1 < c.ncol;
+  constexpr bool full = S::P % S::Y == 0;     // every tile has Y columns
+  const bool va = full || 2 * g < c.ncol, vb = full || 2 * g + 1 < c.ncol;
+  // 0 * s is 0 for finite s and NaN for an infinite or NaN s, so `chk` stays
+  // 0 exactly when every point is finite; the maximum skips NaN
+  T m = T(0), chk = T(0);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
     const T sa = xabs(st.z[0][k2].x) + xabs(st.z[0][k2].y) + xabs(st.z[2][k2].x);
     const T sb = xabs(st.z[1][k2].x) + xabs(st.z[1][k2].y) + xabs(st.z[2][k2].y);
     if (va) {
-      if (!(sa <= big_finite<T>())) st.bad = 1;
-      else st.umax = sa > st.umax ? sa : st.umax;
+      m = xmax(m, sa);
+      chk = chk + T(0) * sa;
     }
     if (vb) {
-      if (!(sb <= big_finite<T>())) st.bad = 1;
-      else st.umax = sb > st.umax ? sb : st.umax;
+      m = xmax(m, sb);
+      chk = chk + T(0) * sb;
     }
   }
+  st.bad = !(chk == T(0)) || !(m <= big_finite<T>());
+  st.umax = m;
 }
 
 // product line f (0..5) of the pair at register position k2:
@@ -203,7 +209,7 @@ NS3D_HD void zfast_fwd1(const ZFastCtx<T, N1, N2>& c, int tid, const ZFastState<
     cplx<T>* X = c.X + (g * 3 + q) * S::LP;
 #pragma unroll
     for (int k = 0; k < N2; ++k)
-      X[k1 * (N2 + 1) + k] = (k == 0 || k1 == 0) ? v[k] : v[k] * c.twf[k * N1 + k1];
+      X[k1 * (N2 + 1) + k] = k == 0 ? v[k] : v[k] * c.twf[k * N1 + k1];   // twf[k N1] = 1
   }
 }
 
@@ -225,43 +231,82 @@ NS3D_HD void zfast_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
   }
 }
 
-// extraction of round r: kz < h of two real lines from each complex line
+// extraction of round r: kz < h of two real lines from each complex line.
+// Thread (kl, grp) with kl = tid % KL, grp = tid / KL (6 groups) takes the
+// lines grp + 6 i (all with q = grp % 3) at k = kl + KL j.
+template <int N1, int N2>
+struct ZExtractShape {
+  static constexpr int H = N1 * N2 / 3;
+  static constexpr int KL = H < 32 ? H : 32;
+  static constexpr int NG = 6;
+  static_assert(ZFastShape<N1, N2>::NTHR == NG * KL, "extraction: 6 groups of KL threads");
+  static_assert((ZFastShape<N1, N2>::NPAIR * 3) % NG == 0, "extraction: whole line groups");
+};
+
 template <typename T, int N1, int N2>
-NS3D_HD void zfast_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr, int r) {
+NS3D_HD void zfast_extract(const ZFastCtx<T, N1, N2>& c, int tid, int r) {
   using S = ZFastShape<N1, N2>;
+  using E = ZExtractShape<N1, N2>;
   const ZArgs<T>& a = *c.a;
   constexpr int h = S::H;
   cplx<T>* out = a.out + c.bz * a.out_bs + c.by * a.xs + (long long)c.y0 * h;
-  for (int t = tid; t < S::NPAIR * 3 * h; t += nthr) {
-    const int k = t % h;
-    const int line = t / h;           // g * 3 + q
-    const int g = line / 3, q = line % 3;
-    const int f = 3 * r + q;
-    const int col = 2 * g + (f & 1);
-    if (col >= c.ncol) continue;
-    const cplx<T>* X = c.X + line * S::LP;
-    const cplx<T> zk = X[zfast_fpos<N1, N2>(k)];
-    const cplx<T> zm = cconj(X[zfast_fpos<N1, N2>((S::P - k) % S::P)]);
-    const cplx<T> s = zk + zm, d = zk - zm;
-    const int comp = 2 * (f >> 1);
-    out[comp * a.out_cs + col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
-    out[(comp + 1) * a.out_cs + col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);
+  const int kl = tid % E::KL, grp = tid / E::KL;
+  const int q = grp % 3, f = 3 * r + q;
+  const int comp = 2 * (f >> 1);
+  cplx<T>* o0 = out + comp * a.out_cs;
+  cplx<T>* o1 = out + (comp + 1) * a.out_cs;
+  constexpr bool full = S::P % S::Y == 0;
+#pragma unroll
+  for (int j = 0; j < h / E::KL; ++j) {
+    const int k = kl + E::KL * j;
+    const int pk = zfast_fpos<N1, N2>(k);
+    const int pm = zfast_fpos<N1, N2>(k == 0 ? 0 : S::P - k);
+#pragma unroll
+    for (int i = 0; i < S::NPAIR * 3 / E::NG; ++i) {
+      const int line = grp + E::NG * i;   // g * 3 + q
+      const int col = 2 * (line / 3) + (f & 1);
+      if (!full && col >= c.ncol) continue;
+      const cplx<T>* X = c.X + line * S::LP;
+      const cplx<T> zk = X[pk];
+      const cplx<T> zm = cconj(X[pm]);
+      const cplx<T> s = zk + zm, d = zk - zm;
+      o0[col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+      o1[col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);
+    }
   }
 }
 
 // Block maximum of the per-thread maxima (in T: FP64 instructions are slow on
 // this part), one atomic per block; a negative entry flags a non-finite value.
+// On the GPU warp 0 reduces (lane-strided, then shuffles); the host emulator
+// calls it once with lane 0 and reduces serially (max and or are exact in any
+// order).
 template <typename T, int N1, int N2>
-NS3D_HD void zfast_reduce(const ZFastCtx<T, N1, N2>& c, const T* red, int nthr) {
+NS3D_HD void zfast_reduce(const ZFastCtx<T, N1, N2>& c, const T* red, int nthr, int lane) {
   const ZArgs<T>& a = *c.a;
   if (!a.ctrl) return;
   T m = T(0);
   int bad = 0;
+#if defined(__CUDA_ARCH__)
+  for (int i = lane; i < nthr; i += 32) {
+    const T r = red[i];
+    bad |= r < T(0);
+    m = r > m ? r : m;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+#else
   for (int i = 0; i < nthr; ++i) {
     const T r = red[i];
     bad |= r < T(0);
     m = r > m ? r : m;
   }
+#endif
+  if (lane != 0) return;
   atomic_max_u64(&a.ctrl[c.bz].umax_bits, dbl_bits((double)m));
   if (bad) atomic_or_i32(&a.ctrl[c.bz].status, NS3D_FLAG_NONFINITE);
 }

@@ -196,3 +196,17 @@ def test_emulated_fused_x_large_tiles(built, N):
         lib.ns3d_hostcheck_use_fast(1)
     assert rel(got, gen) < 2e-6
     assert rel(got, uh) > 1e-6     # the step changed the field
+
+
+@pytest.mark.parametrize("N,val", [(32, np.nan), (64, np.inf), (64, np.nan)])
+def test_emulated_register_z_pass_flags_nonfinite(built, N, val):
+    """A non-finite coefficient reaches every physical point of its line; the
+    register-resident z pass (FP32) flags the member NONFINITE (bit 1)."""
+    prm = S.Params(eps0=1.0)
+    u = I.random_spectrum(N, seed=3, k0=3.0)
+    u[1, 2, 3, 4] = val
+    _, rc, _ = hostcheck(built, u, 3 * N // 2, prm, nsteps=1, dtype=0)
+    assert rc & 1
+    _, rc, _ = hostcheck(built, I.random_spectrum(N, seed=3, k0=3.0), 3 * N // 2, prm, nsteps=1,
+                         dtype=0)
+    assert rc == 0

@@ -235,6 +235,21 @@ def test_device_status_nonfinite_and_unstable(B):
     p.close()
 
 
+@pytest.mark.parametrize("N,val", [(64, np.nan), (256, np.inf)])
+def test_device_status_nonfinite_fp32_register_kernels(B, N, val):
+    """FP32 at the register-resident sizes (z pass with the in-register CFL
+    maximum, fused x pass): a non-finite coefficient sets NONFINITE."""
+    u = I.random_spectrum(N, seed=2, k0=3.0)
+    u[2, 3, 1, 5] = val
+    p = plan(B, [N], B.NS3D_F32, eps0=1.0)
+    p.set_initial(0, u)
+    p.step(1)
+    with pytest.raises(B.Ns3dError) as e:
+        p.synchronize()
+    assert e.value.code == 4
+    p.close()
+
+
 def test_workspace_limit_is_enforced(B):
     with pytest.raises(B.Ns3dError) as e:
         B.Plan([64], B.NS3D_F32, workspace_limit=1 << 20)
