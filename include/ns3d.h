@@ -217,6 +217,19 @@ ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d_params* p,
                                   const void* uhat, void* rhs_out, void* cuda_stream);
 
 /* Static text for a status code. */
+/* Test hook for the failure path of the bounded device waits (no counterpart
+ * in the paper).  While `on` is nonzero, every launch of the fused x pass
+ * (FP32 levels with P = 3N/2, P in {48, 96, 192, 384}) expects 16 bytes more
+ * on its first staged input tile than the tile's copy delivers, so each
+ * block's wait for that tile ends at its time limit (about one second): the
+ * block flags its member TIMEOUT, waits (bounded) for its other copies and
+ * returns; the member's state is then undefined and the next call that reads
+ * the device status returns NS3D_ERR_TIMEOUT.  Nothing faults and the CUDA
+ * context stays usable.  Synchronises the plan's stream.  Returns
+ * NS3D_ERR_NOT_SUPPORTED if no level of the plan runs the fused pass.  Off by
+ * default. */
+ns3d_status ns3d_test_stall_staging(ns3d_plan plan, int on);
+
 const char* ns3d_status_string(ns3d_status s);
 
 #ifdef __cplusplus

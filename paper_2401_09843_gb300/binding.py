@@ -26,7 +26,7 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_set_initial", "ns3d_get_state", "ns3d_step", "ns3d_synchronize",
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
-           "ns3d_eval_rhs_noalloc"]
+           "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging"]
 
 
 class Ns3dError(RuntimeError):
@@ -215,6 +215,12 @@ class Plan:
 
     def synchronize(self):
         _check(self.lib.ns3d_synchronize(self.h), "ns3d_synchronize")
+
+    def test_stall_staging(self, on: bool):
+        """Test hook: the fused x pass's first staged tile never completes,
+        so its bounded waits time out (the next status read reports
+        TIMEOUT).  For tests of the failure path only."""
+        _check(self.lib.ns3d_test_stall_staging(self.h, int(bool(on))), "ns3d_test_stall_staging")
 
     def eval_rhs(self, member: int, uhat):
         x = self._as_dev(uhat, member)

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR, 1)
     const XfTile t = xf_tile<N1, N2>(j, m, a.stage);
     const CUtensorMap* mp = t.src == 0 ? &maps.dq : (t.src == 1 ? &maps.u0 : &maps.us);
     uint64_t* b = bar + j % S::NSLOT;
-    mbar_arrive_expect_tx(b, kTileBytes);
+    mbar_arrive_expect_tx(b, j == 0 ? kTileBytes + a.extra_tx : kTileBytes);
     tma_load_2d(ring + (j % S::NSLOT) * S::SLOT, mp, 2 * bx * S::W, (int)t.row, b);
   };
 

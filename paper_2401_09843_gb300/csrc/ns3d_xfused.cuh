@@ -55,6 +55,7 @@ struct XFusedArgs {
   const cplx<T>* tw;   // exp(-2 pi i e / P)
   const T* lam;        // lambda_k by |k|^2 (integer), 0 .. 3 (h - 1)^2
   int N, h, stage;
+  unsigned extra_tx;   // 0; a test of the timeout path expects more bytes on tile 0
   long long m6, m3, mA;   // member strides of Dq, U, A
   SpecT<T> sp;
   Ns3dCtrl* ctrl;

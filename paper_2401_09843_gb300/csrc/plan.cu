@@ -39,6 +39,7 @@ struct Level {
   bool a_valid = false;   // W1 holds the x-inverse of U0 (set by the last step)
   XFusedMaps maps{};      // TMA descriptors of W2 (Dq), U0, US for the fused x pass
   void* lamT = nullptr;   // lambda_k by |k|^2 (fused levels)
+  unsigned extra_tx = 0;  // test hook: bytes the first staged tile never delivers
 };
 
 struct DeviceGuard {
@@ -184,6 +185,7 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
   b.fused = L.fused && stage >= 1 && m0 == 0 && nm == L.B;
   b.maps = &L.maps;
   b.lam = L.lamT;
+  b.extra_tx = L.extra_tx;
   return enqueue_rhs<T>(b, stage, nm, in, out, want_umax, s, tm);
 }
 
@@ -243,6 +245,7 @@ ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in
     x.ax = W1;
     x.tw = tw;
     x.lam = static_cast<const T*>(b.lam);
+    x.extra_tx = b.extra_tx;
     x.N = g.N;
     x.h = g.h;
     x.stage = stage;
@@ -349,9 +352,10 @@ ns3d_status get_d1(ns3d_plan p, Level& L, const cplx<T>* src, void* dst, int on_
 }
 
 ns3d_status status_of_flags(int flags) {
+  // a timed-out stage leaves its output undefined: report the cause first
+  if (flags & NS3D_FLAG_TIMEOUT) return NS3D_ERR_TIMEOUT;
   if (flags & NS3D_FLAG_NONFINITE) return NS3D_ERR_NONFINITE;
   if (flags & NS3D_FLAG_UNSTABLE) return NS3D_ERR_UNSTABLE_DT;
-  if (flags & NS3D_FLAG_TIMEOUT) return NS3D_ERR_TIMEOUT;
   return NS3D_OK;
 }
 
@@ -573,6 +577,24 @@ extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, 
   }
   L->a_valid = false;   // the evaluation used W1
   if (!on_device) NS3D_CK(cudaStreamSynchronize(p->stream));
+  return NS3D_OK;
+}
+
+extern "C" ns3d_status ns3d_test_stall_staging(ns3d_plan p, int on) {
+  if (!p) return NS3D_ERR_INVALID_ARG;
+  bool any = false;
+  for (Level& L : p->levels) {
+    if (!L.fused) continue;
+    L.extra_tx = on ? 16u : 0u;
+    any = true;
+  }
+  if (!any) return NS3D_ERR_NOT_SUPPORTED;
+  DeviceGuard dg(p->device);
+  NS3D_CK(cudaStreamSynchronize(p->stream));
+  if (p->exec) cudaGraphExecDestroy(p->exec);   // rebuilt with the new launch arguments
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
   return NS3D_OK;
 }
 

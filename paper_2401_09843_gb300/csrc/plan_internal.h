@@ -48,6 +48,7 @@ struct StageBufs {
   bool fused = false;
   const ns3d::XFusedMaps* maps = nullptr;   // TMA descriptors (fused stages)
   const void* lam = nullptr;                 // lambda_k by |k|^2 (fused stages)
+  unsigned extra_tx = 0;                     // test hook (ns3d_test_stall_staging)
 };
 
 // Optional per-kernel timing: events recorded before each kernel kind.
