@@ -238,3 +238,45 @@ def sparse_random(N: int, seed: int, nmodes: int = 40, kmax: int = 0, energy: fl
     uhat = truncate(uhat)
     e = _energy_d1(uhat)
     return uhat * np.sqrt(energy / e) if e > 0 else uhat
+
+
+def sparse_modes(N: int, seed: int, nmodes: int = 40, kmax: int = 0, energy: float = 0.5):
+    """A real divergence-free field given by its nonzero modes, for grids too
+    large to hold densely on the host: returns (K, V), K (n, 3) integer wave
+    vectors as stored in the D1 layout (k_z >= 0; on the k_z = 0 plane both k
+    and -k are listed, with conjugate coefficients) and V (n, 3) complex128
+    coefficients.  Modes are i k x g / |k| for Gaussian g with |k_i| < kmax
+    (default N/2), scaled to the given energy 1/2 sum over the full spectrum."""
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), 101])))
+    h = N // 2
+    kmax = kmax or h
+    acc = {}
+    for _ in range(nmodes):
+        k = rng.integers(-(kmax - 1), kmax, size=3)
+        k[2] = abs(k[2])
+        if not k.any():
+            continue
+        g = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+        v = 1j * np.cross(k, g) / np.linalg.norm(k)
+        key = (int(k[0]), int(k[1]), int(k[2]))
+        acc[key] = acc.get(key, 0) + v
+        if k[2] == 0:
+            mk = (-key[0], -key[1], 0)
+            acc[mk] = acc.get(mk, 0) + np.conj(v)
+    K = np.array(sorted(acc), dtype=np.int64).reshape(-1, 3)
+    V = np.array([acc[tuple(k)] for k in K.tolist()], dtype=np.complex128).reshape(-1, 3)
+    w = np.where(K[:, 2] > 0, 2.0, 1.0)
+    e = 0.5 * float(np.sum(w * np.sum(np.abs(V) ** 2, axis=1)))
+    return K, (V * np.sqrt(energy / e) if e > 0 else V)
+
+
+def modes_of(uhat: np.ndarray, rtol: float = 0.0):
+    """(K, V) of the entries of a D1 array above rtol times its largest (K
+    signed, k_z >= 0); rtol > 0 drops the round-off of a sampled field."""
+    N = uhat.shape[-2]
+    mag = np.max(np.abs(uhat), axis=0)
+    nz = np.nonzero(mag > rtol * np.max(mag)) if rtol > 0 else np.nonzero(np.any(uhat != 0, axis=0))
+    kx = np.where(nz[0] < N // 2, nz[0], nz[0] - N)
+    ky = np.where(nz[1] < N // 2, nz[1], nz[1] - N)
+    K = np.stack([kx, ky, nz[2]], axis=1).astype(np.int64)
+    return K, uhat[:, nz[0], nz[1], nz[2]].T.copy()

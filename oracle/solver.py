@@ -161,7 +161,12 @@ def damped_threshold(N: int, prm: Params) -> int:
 def dissipation(N: int, prm: Params) -> np.ndarray:
     """lambda_k = nu |kappa|^2 + eps_N |kappa|^{2s} Q_k on the D1 grid."""
     kx, ky, kz = wavenumbers(N)
-    k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
+    return dissipation_of_k2((kx * kx + ky * ky + kz * kz).astype(np.float64), N, prm)
+
+
+def dissipation_of_k2(k2: np.ndarray, N: int, prm: Params) -> np.ndarray:
+    """lambda_k as a function of the integer |k|^2 (eq. shv_disc constants)."""
+    k2 = np.asarray(k2, dtype=np.float64)
     a2 = (TWO_PI / prm.L) ** 2
     kap2 = a2 * k2
     eps_N = prm.eps0 * float(N) ** (1.0 - 2.0 * prm.s)
@@ -368,3 +373,37 @@ def rhs_by_convolution(uhat: np.ndarray, prm: Params) -> np.ndarray:
     N = uhat.shape[-2]
     b = nonlinear_by_convolution(uhat, prm)
     return (leray(b, prm.L) - dissipation(N, prm) * uhat) * retained_mask(N)
+
+
+def rhs_sparse(K: np.ndarray, V: np.ndarray, N: int, prm: Params):
+    """R(u_hat) for a field given by its nonzero modes (K integer wave vectors
+    with k_z >= 0 as stored in the D1 layout, V their coefficients), at any N
+    without a grid: the Galerkin sum of ``nonlinear_by_convolution`` over mode
+    pairs, evaluated only at the modes it reaches in K_N, the Leray
+    projection, and -lambda_k u_hat_k at the input modes.  Returns (Kout, R):
+    every mode where R can be nonzero (k_z >= 0) and R there."""
+    h = N // 2
+    K = np.asarray(K, dtype=np.int64).reshape(-1, 3)
+    V = np.asarray(V, dtype=np.complex128).reshape(-1, 3)
+    pos = K[:, 2] > 0                                  # a stored k_z > 0 mode stands for -k too
+    Kf = np.concatenate([K, -K[pos]])
+    Vf = np.concatenate([V, np.conj(V[pos])])
+    ksum = (Kf[:, None, :] + Kf[None, :, :]).reshape(-1, 3)
+    ii, jj = np.divmod(np.arange(len(Kf) ** 2), len(Kf))
+    keep = (np.abs(ksum[:, 0]) < h) & (np.abs(ksum[:, 1]) < h) & (ksum[:, 2] >= 0) & (ksum[:, 2] < h)
+    ks, ii, jj = ksum[keep], ii[keep], jj[keep]
+    inband = np.all(np.abs(K[:, :2]) < h, axis=1) & (K[:, 2] < h)
+    Kout, inv = np.unique(np.concatenate([ks, K[inband]]), axis=0, return_inverse=True)
+    inv = inv.reshape(-1)
+    Bsum = np.zeros((len(Kout), 3, 3), dtype=np.complex128)
+    np.add.at(Bsum, inv[:len(ks)], Vf[ii][:, :, None] * Vf[jj][:, None, :])
+    kap = (TWO_PI / prm.L) * Kout.astype(np.float64)
+    b = -1j * np.einsum("nl,njl->nj", kap, Bsum)
+    k2 = np.sum(kap * kap, axis=1)
+    safe = np.where(k2 > 0, k2, 1.0)
+    R = b - kap * (np.sum(kap * b, axis=1) / safe)[:, None]
+    R[k2 == 0] = 0.0
+    kin = Kout[inv[len(ks):]]
+    lam = dissipation_of_k2(np.sum(kin * kin, axis=1), N, prm)
+    np.add.at(R, inv[len(ks):], -lam[:, None] * V[inband])
+    return Kout, R
