@@ -14,7 +14,7 @@ struct DevSync {
 };
 
 template <typename T, int SIGN, bool CF1, bool CFL>
-__global__ void __launch_bounds__(256) k_col(ColArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) k_col(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   colfft_block<T, SIGN, CF1, CFL>(a, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, blockDim.x,
                                   reinterpret_cast<cplx<T>*>(ns3d_smem), DevSync{});

@@ -5,8 +5,9 @@
 
 namespace ns3d {
 
+// 512 threads (FP32) when a tile's shared memory allows one block per SM
 template <typename T>
-__global__ void __launch_bounds__(128) k_zfused(ZArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 128) k_zfused(ZArgs<T> a) {
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
   double* red = reinterpret_cast<double*>(sm + 4 * a.P * a.ldw);

@@ -71,6 +71,7 @@ struct Geom {
 };
 
 constexpr size_t kSmemTarget = 113 * 1024;   // two blocks per SM
+constexpr size_t kSmemMax = 227 * 1024;      // one block per SM
 
 inline int col_width(int n, int npass, int esz, int W0, size_t* smem) {
   int W = W0;
@@ -100,12 +101,21 @@ inline bool make_geom(int N, int P, int esz, Geom* g) {
   if (!make_fft_plan(N, &g->plN)) g->plN.npass = 0;
   const int W0 = esz == 8 ? 16 : 8;
   g->Wc = col_width(P, g->plP.npass, esz, W0, &g->smem_c);
+  // long FP32 lines: fewer than 4 columns (16-byte row segments) at two blocks
+  // per SM; take 4 columns at one block of 512 threads instead
+  if (esz == 8 && g->Wc < 4 && g->plP.npass >= 2 && (size_t)2 * P * 5 * esz <= kSmemMax) {
+    g->Wc = 4;
+    g->smem_c = (size_t)2 * P * 5 * esz;
+    g->nthr_c = 512;
+  }
   g->ldwc = g->Wc + 1;
   g->WcN = g->plN.npass ? col_width(N, g->plN.npass, esz, W0, &g->smem_cN) : 1;
   g->ldwcN = g->WcN + 1;
   int Wz = esz == 8 ? 8 : 4;
   auto needz = [&](int w) { return (size_t)4 * P * (w + 1) * esz + (size_t)8 * g->nthr_z; };
   while (Wz > 2 && needz(Wz) > kSmemTarget) Wz /= 2;
+  // one block per SM anyway: FP32 runs 512 threads instead of 128
+  if (esz == 8 && needz(Wz) > kSmemTarget) g->nthr_z = 512;
   g->Wz = Wz;
   g->ldwz = Wz + 1;
   g->smem_z = needz(Wz);
