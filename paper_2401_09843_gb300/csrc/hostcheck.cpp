@@ -13,10 +13,18 @@
 #include "ns3d_zfast.cuh"
 #include "ns3d_colfast.cuh"
 #include "ns3d_xfused.cuh"
+#include "ns3d_colfast3.cuh"
+#include "ns3d_zfast3.cuh"
 
 namespace {
 
-bool g_use_fast = true;
+// 0: generic kernels only; 1: the register-resident kernels the GPU uses;
+// 2: as 1 but the three-pass kernels at the test factorisations below
+int g_use_fast = 1;
+
+// three-pass factorisations emulated at short lengths (the GPU builds them
+// for long lines only), so that their index logic meets the oracle
+#define NS3D_FOR_LONG_TEST(X) X(4, 3, 4) X(6, 4, 4) X(8, 4, 6) X(8, 6, 8)
 
 struct HostSync {
   void operator()() const {}
@@ -60,10 +68,41 @@ void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
       }
 }
 
+template <typename T, int SIGN, int N1, int N2, int N3>
+void run_colfast3(const ColArgs<T>& a, int gy, int gz) {
+  using S = ColFast3Shape<N1, N2, N3>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  const int gx = (a.ncols + S::W - 1) / S::W;
+  for (int z = 0; z < gz; ++z)
+    for (int y = 0; y < gy; ++y)
+      for (int x = 0; x < gx; ++x) {
+        const int ncol = std::min(S::W, a.ncols - x * S::W);
+        for (int t = 0; t < S::NTHR; ++t) colfast3_twiddles<T, SIGN, S::P>(sm.data(), a.tw, t, S::NTHR);
+        cplx<T>* X = sm.data() + S::P;
+        for (int t = 0; t < S::NTHR; ++t)
+          colfast3_pass1<T, SIGN, N1, N2, N3, (SIGN > 0)>(a, x, y, z, t, S::NTHR, sm.data(), X);
+        for (int t = 0; t < S::NTHR; ++t) colfast3_pass2<T, SIGN, N1, N2, N3>(t, S::NTHR, ncol, sm.data(), X);
+        for (int t = 0; t < S::NTHR; ++t)
+          colfast3_pass3<T, SIGN, N1, N2, N3, (SIGN < 0)>(a, x, y, z, t, S::NTHR, X);
+      }
+}
+
 template <typename T, int SIGN, bool CF1, bool CFL>
 void run_col(const ColArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   const bool padded_inverse = SIGN > 0 && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
   const bool truncated_forward = SIGN < 0 && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
+  if (g_use_fast && sizeof(T) == 4 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
+#define NS3D_HC_CF3(A, B, C)                              \
+    if (a.pl.n == (A) * (B) * (C)) {                      \
+      run_colfast3<T, SIGN, A, B, C>(a, L.gy, L.gz);      \
+      return;                                             \
+    }
+    NS3D_FOR_COLFAST3(NS3D_HC_CF3)
+    if (g_use_fast == 2) {
+      NS3D_FOR_LONG_TEST(NS3D_HC_CF3)
+    }
+#undef NS3D_HC_CF3
+  }
   if (g_use_fast && sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n &&
       (padded_inverse || truncated_forward)) {
 #define NS3D_HC_CF(A, B)                        \
@@ -115,9 +154,65 @@ void run_zfast(const ZArgs<T>& a, int nm) {
       }
 }
 
+// The three-pass z pass as one persistent block running every tile (rows
+// x < nx of each member), phase by phase and thread by thread.
+template <typename T, int N1, int N2, int N3>
+void run_zfast3(const ZArgs<T>& a, int nm, int nx) {
+  using S = ZFast3Shape<N1, N2, N3>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<T> red(S::NTHR);
+  std::vector<ZFast3State<T, N1, N2, N3>> st(S::NTHR);
+  for (int t = 0; t < S::NTHR; ++t) zfast3_twiddles<T, N1, N2, N3>(a, sm.data(), t, S::NTHR);
+  for (auto& x : st) {
+    x.umax = T(0);
+    x.chk = T(0);
+  }
+  int cur = -1;
+  auto flush = [&]() {
+    if (cur < 0 || !a.ctrl) return;
+    for (int t = 0; t < S::NTHR; ++t) red[t] = zfast3_red_value(st[t]);
+    zfast3_flush<T>(a, cur, red.data(), S::NTHR, 0);
+  };
+  const long long ntiles = (long long)nm * S::P * (S::P / 2);
+  for (long long t = 0; t < ntiles; ++t) {
+    int bz, by, y0;
+    zfast3_tile<N1, N2, N3>(t, &bz, &by, &y0);
+    if (by >= nx) continue;
+    if (bz != cur) {
+      flush();
+      for (auto& x : st) {
+        x.umax = T(0);
+        x.chk = T(0);
+      }
+      cur = bz;
+    }
+    const ZFast3Ctx<T, N1, N2, N3> c = zfast3_ctx<T, N1, N2, N3>(a, bz, by, y0, sm.data());
+    for (int i = 0; i < S::NTHR; ++i) zfast3_inv1(c, i, S::NTHR);
+    for (int i = 0; i < S::NTHR; ++i) zfast3_inv2(c, i, S::NTHR);
+    for (int i = 0; i < S::NTHR; ++i) zfast3_inv3(c, i, st[i]);
+    for (int r = 0; r < 2; ++r) {
+      for (int i = 0; i < S::NTHR; ++i) zfast3_fwdA(c, i, st[i], r);
+      for (int i = 0; i < S::NTHR; ++i) zfast3_fwdB(c, i, S::NTHR);
+      for (int i = 0; i < S::NTHR; ++i) zfast3_fwdC(c, i, S::NTHR);
+      for (int i = 0; i < S::NTHR; ++i) zfast3_extract(c, i, S::NTHR, r);
+    }
+  }
+  flush();
+}
+
 template <typename T>
 bool run_z_fast_if_any(const ZArgs<T>& a, int P) {
   if (sizeof(T) != 4 || 3 * a.h != P) return false;
+#define NS3D_HC_ZF3(A, B, C)           \
+  if (P == (A) * (B) * (C)) {          \
+    run_zfast3<T, A, B, C>(a, 1, P);   \
+    return true;                       \
+  }
+  NS3D_FOR_ZFAST3(NS3D_HC_ZF3)
+  if (g_use_fast == 2) {
+    NS3D_FOR_LONG_TEST(NS3D_HC_ZF3)
+  }
+#undef NS3D_HC_ZF3
 #define NS3D_HC_ZF(A, B)               \
   if (P == (A) * (B)) {                \
     run_zfast<T, A, B>(a, 1);          \
@@ -314,7 +409,54 @@ int ns3d_hostcheck_run(int dtype, int N, int P, const double* prm, const void* u
 }
 
 // 0: emulate the generic tile z pass even where a register-resident one exists.
-void ns3d_hostcheck_use_fast(int on) { g_use_fast = on != 0; }
+void ns3d_hostcheck_use_fast(int mode) { g_use_fast = mode; }
+
+// One column pass of the three-pass kernel at P = 1536 (N = 1024) on a
+// [rows][ncols] array: sign > 0 the padded inverse (N rows in, P out),
+// sign < 0 the truncated forward (P rows in, N out, Nyquist row zero).
+int ns3d_hostcheck_colpass3(int sign, const void* in, void* out, int ncols) {
+  constexpr int P = 16 * 12 * 8, N = 2 * P / 3, h = N / 2;
+  const std::vector<cplx<float>> tw = ns3d::make_twiddles<float>(P);
+  ColArgs<float> a{};
+  a.in = static_cast<const cplx<float>*>(in);
+  a.out = static_cast<cplx<float>*>(out);
+  a.tw = tw.data();
+  a.pl.n = P;
+  a.h = h;
+  a.ncols = ncols;
+  a.in_cs = a.out_cs = 1;
+  a.in_rs = a.out_rs = ncols;
+  a.scale = 1.0f;
+  if (sign > 0) {
+    a.nrow_in = N; a.nrow_out = P; a.pad_in = 1; a.trunc_out = 0;
+    run_colfast3<float, +1, 16, 12, 8>(a, 1, 1);
+  } else {
+    a.nrow_in = P; a.nrow_out = N; a.pad_in = 0; a.trunc_out = 1;
+    run_colfast3<float, -1, 16, 12, 8>(a, 1, 1);
+  }
+  return 0;
+}
+
+// The three-pass z pass at P = 1536 on rows x < nx of Bq-like input
+// [3][nx][P][h] -> Cq-like output [6][nx][P][h]; returns the status flags and
+// the CFL maximum.
+int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
+  constexpr int P = 16 * 12 * 8, h = P / 3;
+  const std::vector<cplx<float>> tw = ns3d::make_twiddles<float>(P);
+  Ns3dCtrl ctrl{};
+  ZArgs<float> a{};
+  a.in = static_cast<const cplx<float>*>(in);
+  a.out = static_cast<cplx<float>*>(out);
+  a.tw = tw.data();
+  a.P = P;
+  a.h = h;
+  a.in_cs = a.out_cs = (long long)nx * P * h;
+  a.xs = (long long)P * h;
+  a.ctrl = &ctrl;
+  run_zfast3<float, 16, 12, 8>(a, 1, nx);
+  std::memcpy(umax, &ctrl.umax_bits, sizeof(double));
+  return ctrl.status;
+}
 
 // Radix plan chosen for length n (for tests).
 int ns3d_hostcheck_plan(int n, int* radix, int maxp) {

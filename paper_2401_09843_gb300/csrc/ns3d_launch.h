@@ -10,6 +10,8 @@
 #include "ns3d_zfast.cuh"
 #include "ns3d_colfast.cuh"
 #include "ns3d_xfused.cuh"
+#include "ns3d_colfast3.cuh"
+#include "ns3d_zfast3.cuh"
 
 namespace ns3d {
 
@@ -31,12 +33,28 @@ cudaError_t colfast_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s)
 template <typename T, int SIGN, int N1, int N2>
 cudaError_t colfast_init();
 
+template <typename T, int SIGN, int N1, int N2, int N3>
+cudaError_t colfast3_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s);
+template <typename T, int N1, int N2, int N3>
+cudaError_t zfast3_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2, int N3>
+cudaError_t long_init();
+
 // A column pass: the register-resident kernel where one exists for (T, n, tile
-// width 16), the generic tile kernel otherwise.
+// width 16) or the three-pass one for long n, the generic tile kernel otherwise.
 template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaStream_t s) {
   const bool padded_inverse = kind == COL_INV_CC && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
   const bool truncated_forward = kind == COL_FWD_CC && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
+  if (sizeof(T) == 4 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
+    const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
+#define NS3D_CF3_GO(A, B, C)                                                        \
+    if (a.pl.n == (A) * (B) * (C))                                                  \
+      return kind == COL_INV_CC ? colfast3_launch<float, +1, A, B, C>(af, L, s)    \
+                                : colfast3_launch<float, -1, A, B, C>(af, L, s);
+    NS3D_FOR_COLFAST3(NS3D_CF3_GO)
+#undef NS3D_CF3_GO
+  }
   if (sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
     const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
 #define NS3D_CF_GO(A, B)                                                          \
@@ -100,6 +118,16 @@ cudaError_t zfast_init();
 
 
 template <typename T>
+bool zfast3_available(int P) {
+  if (sizeof(T) != 4) return false;
+#define NS3D_ZF3_CASE(A, B, C) \
+  if (P == (A) * (B) * (C)) return true;
+  NS3D_FOR_ZFAST3(NS3D_ZF3_CASE)
+#undef NS3D_ZF3_CASE
+  return false;
+}
+
+template <typename T>
 bool zfast_available(int P) {
   if (sizeof(T) != 4) return false;
 #define NS3D_ZF_CASE(A, B) \
@@ -138,6 +166,13 @@ cudaError_t kernels_init() {
     }
     NS3D_FOR_ZFAST(NS3D_ZF_INIT)
 #undef NS3D_ZF_INIT
+#define NS3D_LONG_INIT(A, B, C)                             \
+    {                                                       \
+      cudaError_t r = long_init<float, A, B, C>();          \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_ZFAST3(NS3D_LONG_INIT)
+#undef NS3D_LONG_INIT
 #define NS3D_XF_INIT(A, B)                                  \
     {                                                       \
       cudaError_t r = xfused_init<float, A, B>();           \

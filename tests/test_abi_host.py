@@ -210,3 +210,78 @@ def test_emulated_register_z_pass_flags_nonfinite(built, N, val):
     _, rc, _ = hostcheck(built, I.random_spectrum(N, seed=3, k0=3.0), 3 * N // 2, prm, nsteps=1,
                          dtype=0)
     assert rc == 0
+
+
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_emulated_three_pass_kernels_match_oracle(built, N):
+    """The three-pass column and z kernels (the GPU builds them for P = 1536),
+    emulated at short lengths P = 48 = 4x3x4, 96 = 6x4x4, 192 = 8x4x6 thread by
+    thread: the RHS of a sparse field against the Galerkin product, and CFL
+    steps against the oracle."""
+    prm = S.Params(nu=0.01, eps0=1.0)
+    uh = I.sparse_random(N, seed=N + 3, nmodes=24)
+    ref = S.rhs_by_convolution(uh, prm)
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_use_fast(2)
+    try:
+        got, rc, _ = hostcheck(built, uh, 3 * N // 2, prm, dtype=0)
+        assert rc == 0 and rel(got, ref) < 2e-6
+        if N <= 64:
+            u0 = I.random_spectrum(N, seed=N, k0=3.0)
+            sref, tref, _ = S.integrate(u0, prm, 2)
+            got, rc, t = hostcheck(built, u0, 3 * N // 2, prm, nsteps=2, dtype=0)
+            assert rc == 0 and abs(t - tref) < 1e-6 * tref
+            assert rel(got, sref) < 2e-5
+    finally:
+        lib.ns3d_hostcheck_use_fast(1)
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_three_pass_column_block_1536(built, sign):
+    """One column pass of the P = 1536 = 16x12x8 kernel (N = 1024), emulated:
+    the padded inverse and the truncated forward against numpy's FFT, over a
+    full 16-column tile and a ragged one."""
+    P, N, h, ncols = 1536, 1024, 512, 21
+    rng = np.random.default_rng(5)
+    nin = N if sign > 0 else P
+    x = (rng.standard_normal((nin, ncols)) + 1j * rng.standard_normal((nin, ncols))).astype(np.complex64)
+    out = np.zeros((P if sign > 0 else N, ncols), np.complex64)
+    lib = ctypes.CDLL(built.HOSTLIB)
+    assert lib.ns3d_hostcheck_colpass3(sign, x.ctypes.data_as(ctypes.c_void_p),
+                                       out.ctypes.data_as(ctypes.c_void_p), ncols) == 0
+    xd = x.astype(np.complex128)
+    if sign > 0:
+        full = np.zeros((P, ncols), complex)
+        full[:h] = xd[:h]
+        full[P - N + h + 1:] = xd[h + 1:]       # rows h+1 .. N-1 are k = row - N
+        ref = np.fft.ifft(full, axis=0) * P
+    else:
+        X = np.fft.fft(xd, axis=0)
+        ref = np.zeros((N, ncols), complex)
+        ref[:h] = X[:h]
+        ref[h + 1:] = X[P - N + h + 1:]
+    assert rel(out, ref) < 5e-6
+
+
+def test_three_pass_z_block_1536(built):
+    """The P = 1536 fused z pass on two x rows of a random Bq-like array,
+    emulated: c2r of the three components, the six products, r2c truncated to
+    kz < 512, against numpy's real FFTs; the CFL maximum too."""
+    P, h, nx = 1536, 512, 2
+    rng = np.random.default_rng(6)
+    shape = (3, nx, P, h)
+    bq = ((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(P)).astype(np.complex64)
+    out = np.zeros((6, nx, P, h), np.complex64)
+    umax = ctypes.c_double()
+    lib = ctypes.CDLL(built.HOSTLIB)
+    rc = lib.ns3d_hostcheck_zpass3(bq.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                   nx, ctypes.byref(umax))
+    assert rc == 0
+    spec = np.zeros((3, nx, P, P // 2 + 1), complex)
+    spec[..., :h] = bq
+    u = np.fft.irfft(spec, n=P, axis=-1) * P          # ignores Im of kz = 0
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    ref = np.stack([np.fft.rfft(u[j] * u[l], axis=-1)[..., :h] for j, l in pairs])
+    assert rel(out, ref) < 5e-6
+    umax_ref = np.max(np.abs(u[0]) + np.abs(u[1]) + np.abs(u[2]))
+    assert abs(umax.value - umax_ref) < 1e-5 * umax_ref
