@@ -15,7 +15,8 @@
 namespace ns3d {
 
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR, 1)
+__global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR,
+                                  XFusedShape<N1, N2>::NTHR <= 192 ? 384 / XFusedShape<N1, N2>::NTHR : 1)
     k_xfused(const XFusedArgs<T> a, const __grid_constant__ XFusedMaps maps) {
   using S = XFusedShape<N1, N2>;
   extern __shared__ __align__(128) unsigned char ns3d_smem[];

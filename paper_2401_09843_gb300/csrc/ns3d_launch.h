@@ -90,7 +90,7 @@ cudaError_t xfused_init();
 // The fused x pass exists for FP32 at P = N1 N2 with the default padding.
 template <typename T>
 bool xfused_available(const Geom& g) {
-  if (sizeof(T) != 4 || 3 * g.h != g.P || (g.N * g.h) % 16 != 0) return false;
+  if (sizeof(T) != 4 || 3 * g.h != g.P || (g.N * g.h) % kXfusedW != 0) return false;
 #define NS3D_XF_CASE(A, B) \
   if (g.P == (A) * (B)) return true;
   NS3D_FOR_XFUSED(NS3D_XF_CASE)

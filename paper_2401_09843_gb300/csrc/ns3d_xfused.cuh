@@ -30,11 +30,14 @@
 
 #define NS3D_FOR_XFUSED(X) X(24, 16) X(12, 16) X(12, 8) X(6, 8)
 
+// (ky, kz) columns per CTA; also the width of the TMA boxes (xfused_maps.cu)
+constexpr int kXfusedW = 16;
+
 template <int N1, int N2>
 struct XFusedShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;         // N / 2: rows of one staged tile
-  static constexpr int W = 16;            // (ky, kz) columns per CTA
+  static constexpr int W = kXfusedW;
   static constexpr int NTHR = W * N1;     // one pass-2 task (column, k1) per thread
   static constexpr int LP = P + 1;
   static constexpr int NSLOT = 9;         // staging ring: three product components

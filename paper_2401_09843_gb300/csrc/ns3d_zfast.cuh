@@ -232,14 +232,15 @@ NS3D_HD void zfast_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
 }
 
 // extraction of round r: kz < h of two real lines from each complex line.
-// Thread (kl, grp) with kl = tid % KL, grp = tid / KL (6 groups) takes the
-// lines grp + 6 i (all with q = grp % 3) at k = kl + KL j.
+// Thread (kl, grp) with kl = tid % KL, grp = tid / KL (6 groups of KL = NTHR/6)
+// takes the lines grp + 6 i (all with q = grp % 3) at k = kl + KL j.
 template <int N1, int N2>
 struct ZExtractShape {
   static constexpr int H = N1 * N2 / 3;
-  static constexpr int KL = H < 32 ? H : 32;
   static constexpr int NG = 6;
-  static_assert(ZFastShape<N1, N2>::NTHR == NG * KL, "extraction: 6 groups of KL threads");
+  static constexpr int KL = ZFastShape<N1, N2>::NTHR / NG;
+  static_assert(ZFastShape<N1, N2>::NTHR == NG * KL && H % KL == 0,
+                "extraction: 6 groups of KL threads, KL dividing h");
   static_assert((ZFastShape<N1, N2>::NPAIR * 3) % NG == 0, "extraction: whole line groups");
 };
 

@@ -25,13 +25,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // FP32 complex array [rows][ncols] viewed as floats [rows][2 ncols]; boxes of
-// box_rows rows x 16 complex (128 bytes)
+// box_rows rows x kXfusedW complex (the kernel's tile width: its staged slots
+// and expected byte counts follow from the same constant)
 bool rows_map(CUtensorMap* map, const void* base, long long rows, long long ncols, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc || box_rows < 1 || box_rows > 256) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * ncols), (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(ncols * 8)};
-  const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+  static_assert((2 * kXfusedW * sizeof(float)) % 16 == 0, "TMA box rows: multiples of 16 bytes");
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * kXfusedW), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
