@@ -31,7 +31,7 @@
 #define NS3D_FOR_XFUSED(X) X(24, 16) X(12, 16) X(12, 8) X(6, 8)
 
 // (ky, kz) columns per CTA; also the width of the TMA boxes (xfused_maps.cu)
-constexpr int kXfusedW = 16;
+constexpr int kXfusedW = 8;
 
 template <int N1, int N2>
 struct XFusedShape {

@@ -42,7 +42,7 @@ template <int N1, int N2>
 struct ZFastShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;                     // N/2 of the default padding P = 3N/2
-  static constexpr int NPAIR = (N1 >= 24) ? 8 : 16;   // pairs per CTA
+  static constexpr int NPAIR = (N1 >= 24) ? 4 : 16;   // pairs per CTA
   static constexpr int NTHR = NPAIR * N1;
   static constexpr int Y = 2 * NPAIR;                 // columns per CTA
   // Exchange rows are padded by one element so that the strided pass stores
