@@ -63,8 +63,10 @@ void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < gx; ++x) {
         colfast_twiddles<T, SIGN, N1, N2>(sm.data(), a.tw, 0, 1);
-        colfast_pass1<T, SIGN, N1, N2, (SIGN > 0)>(a, x, y, z, 0, 1, sm.data(), sm.data() + S::P);
-        colfast_pass2<T, SIGN, N1, N2, (SIGN < 0)>(a, x, y, z, 0, 1, sm.data() + S::P);
+        for (int t = 0; t < S::NTHR; ++t)
+          colfast_pass1<T, SIGN, N1, N2, (SIGN > 0)>(a, x, y, z, t, S::NTHR, sm.data(), sm.data() + S::P);
+        for (int t = 0; t < S::NTHR; ++t)
+          colfast_pass2<T, SIGN, N1, N2, (SIGN < 0)>(a, x, y, z, t, S::NTHR, sm.data() + S::P);
       }
 }
 
