@@ -20,6 +20,7 @@ code to run): each step is one RK3 step of the oracle at 32^3.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -156,6 +157,103 @@ def bench_largest(B, torch, cases=((1024, "f32", 4), (768, "f64", 2))):
             torch.cuda.empty_cache()
         out.append(rec)
     return out
+
+
+def cufft_pipeline(torch, N: int, L: float = 2 * math.pi, nu: float = 0.0, s: float = 1.5,
+                   theta: float = 0.5, eps0: float = 1.0, dev: str = "cuda"):
+    """Comparison only, not the product: the same right-hand side written with
+    torch.fft (cuFFT) and element-wise torch kernels in FP32 -- zero-pad to
+    P = 3N/2, c2r, the six products, r2c, truncate, -i kappa . B, Leray,
+    dissipation.  Returns rhs(u) for D1-layout complex64 tensors."""
+    P, h = 3 * N // 2, N // 2
+    k = torch.fft.fftfreq(N, 1.0 / N, device=dev, dtype=torch.float64)
+    kz = torch.arange(h + 1, device=dev, dtype=torch.float64)
+    KX, KY, KZ = torch.meshgrid(k, k, kz, indexing="ij")
+    k2 = KX * KX + KY * KY + KZ * KZ
+    a = 2 * math.pi / L
+    kap = torch.stack([a * KX, a * KY, a * KZ]).to(torch.float32)
+    kap2 = (a * a * k2)
+    mN2 = float(N) ** (2 * theta)
+    epsN = eps0 * float(N) ** (1 - 2 * s)
+    q = torch.where(k2 > math.floor(mN2 * (1 + 1e-12)),
+                    1 - (mN2 / torch.clamp(k2, min=1.0)) ** ((2 * s - 1) / (2 * theta)),
+                    torch.zeros_like(k2))
+    lam = (nu * kap2 + epsN * kap2 ** s * q).to(torch.float32)
+    keep = ((KX.abs() < h) & (KY.abs() < h) & (KZ < h)).to(torch.float32)
+    inv_k2 = torch.where(k2 > 0, 1.0 / torch.clamp(kap2, min=1e-300), torch.zeros_like(kap2)).to(torch.float32)
+    rows = torch.cat([torch.arange(h, device=dev), torch.arange(P - h + 1, P, device=dev)])
+    src = torch.cat([torch.arange(h, device=dev), torch.arange(N - h + 1, N, device=dev)])
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+
+    def rhs(u):
+        U = torch.zeros((3, P, P, P // 2 + 1), dtype=torch.complex64, device=dev)
+        U[:, rows[:, None], rows[None, :], :h] = u[:, src[:, None], src[None, :], :h]
+        phys = torch.fft.irfftn(U, s=(P, P, P), norm="forward")
+        del U
+        Bh = torch.zeros((3, 3) + u.shape[1:], dtype=torch.complex64, device=dev)
+        for j, l in pairs:
+            F = torch.fft.rfftn(phys[j] * phys[l], norm="forward")
+            Bh[j, l, src[:, None], src[None, :], :h] = F[rows[:, None], rows[None, :], :h]
+            if j != l:
+                Bh[l, j] = Bh[j, l]
+        b = -1j * (kap[None, 0] * Bh[:, 0] + kap[None, 1] * Bh[:, 1] + kap[None, 2] * Bh[:, 2])
+        kb = (kap[0] * b[0] + kap[1] * b[1] + kap[2] * b[2]) * inv_k2
+        return (b - kap * kb[None] - lam[None] * u) * keep[None]
+
+    return rhs
+
+
+def bench_cufft(torch, N: int = 256, steps: int = 5):
+    """Timing of the cuFFT pipeline above, one SSP-RK3 step = three rhs calls
+    (fixed dt, so no CFL reduction is timed)."""
+    import ns3d_inputs as I
+    rhs = cufft_pipeline(torch, N)
+    u = torch.from_numpy(I.random_spectrum(N, seed=20240001)).to("cuda", torch.complex64)
+    dt = 1e-3
+
+    def step(u):
+        u1 = u + dt * rhs(u)
+        u2 = 0.75 * u + 0.25 * (u1 + dt * rhs(u1))
+        return u / 3.0 + (2.0 / 3.0) * (u2 + dt * rhs(u2))
+
+    u = step(u)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        u = step(u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"kind": "comparison (torch.fft = cuFFT + element-wise torch kernels, FP32), not the product",
+            "N": N, "steps": steps, "ms_per_step": ms, "value": N ** 3 / (ms * 1e-3), "unit": UNIT}
+
+
+def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
+    """Band-energy gradient (8 <= |k| < 16 at step `nsteps`, checkpoints every
+    `every` steps, fixed dt) at 128^3: wall time of one gradient, forward
+    recomputation included, against `nsteps` forward steps."""
+    import ns3d_inputs as I
+    out = {}
+    for dt_name, dtype in (("f32", B.NS3D_F32), ("f64", B.NS3D_F64)):
+        plan = B.Plan([N], dtype, eps0=1.0, dt_fixed=0.005)
+        plan.set_initial(0, I.random_spectrum(N, seed=20240004))
+        plan.grad_band_energy(0, 8.0, 16.0, 2, checkpoint_every=2)     # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=every)
+        torch.cuda.synchronize()
+        tg = time.perf_counter() - t0
+        plan.step(2)
+        plan.synchronize()
+        t0 = time.perf_counter()
+        plan.step(nsteps)
+        plan.synchronize()
+        tf = time.perf_counter() - t0
+        plan.close()
+        out[dt_name] = {"gradient_s": tg, "forward_s": tf, "ratio": tg / tf}
+    return {"N": N, "steps": nsteps, "checkpoint_every": every, **out}
 
 
 def parse():
@@ -487,6 +585,8 @@ def main():
         line["batched_ensemble"] = bench_ensemble(B, torch, steps=10, warmup=2)
         line["plain_fp64"] = bench_plain_fp64(B, torch, N, steps=3)
         line["largest"] = bench_largest(B, torch)
+        line["cufft_pipeline"] = bench_cufft(torch, N)
+        line["adjoint"] = bench_adjoint(B, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

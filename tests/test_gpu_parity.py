@@ -275,3 +275,16 @@ def test_fp32_path_tracks_fp64_at_256(B):
     assert rel(res[B.NS3D_F32][0], res[B.NS3D_F64][0]) < TOL32
     assert rel(res[B.NS3D_F32][1], res[B.NS3D_F64][1]) < TOL32
     assert abs(res[B.NS3D_F32][2] - res[B.NS3D_F64][2]) < 1e-6 * res[B.NS3D_F64][2]
+
+
+def test_cufft_comparison_pipeline_matches_oracle(B):
+    """The cuFFT pipeline the bench times for comparison computes the same RHS
+    (so the comparison times the same work)."""
+    import torch
+    import bench
+    N = 32
+    prm = S.Params(eps0=1.0)
+    uh = I.random_spectrum(N, seed=3, k0=3.0)
+    rhs = bench.cufft_pipeline(torch, N)
+    got = rhs(torch.from_numpy(uh).to("cuda", torch.complex64)).cpu().numpy()
+    assert rel(got, S.rhs(uh, prm)) < TOL32
