@@ -7,7 +7,8 @@
 namespace ns3d {
 
 template <typename T, int SIGN, int N1, int N2>
-__global__ void __launch_bounds__(ColFastShape<N1, N2>::NTHR) k_colfast(ColArgs<T> a) {
+__global__ void __launch_bounds__(ColFastShape<N1, N2>::NTHR, ColFastShape<N1, N2>::MINB)
+    k_colfast(ColArgs<T> a) {
   using S = ColFastShape<N1, N2>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(ns3d_smem);

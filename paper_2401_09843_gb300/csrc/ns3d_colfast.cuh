@@ -28,7 +28,8 @@ struct ColFastShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;        // N/2 of the default padding P = 3N/2
   static constexpr int W = 16;           // columns per CTA
-  static constexpr int NTHR = 128;
+  static constexpr int NTHR = 256;
+  static constexpr int MINB = 4;         // 32 warps per SM (shared memory allows 4 blocks)
   static constexpr int LP = P + 1;
   static constexpr int SM_ELEMS = P + W * LP;
 };
