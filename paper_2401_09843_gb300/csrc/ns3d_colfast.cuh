@@ -28,8 +28,9 @@ struct ColFastShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;        // N/2 of the default padding P = 3N/2
   static constexpr int W = 16;           // columns per CTA
-  static constexpr int NTHR = 256;
-  static constexpr int MINB = 4;         // 32 warps per SM (shared memory allows 4 blocks)
+  // one pass-2 task per thread at radix 24 (36 warps per SM), else 256 (32 warps)
+  static constexpr int NTHR = N1 >= 24 ? 384 : 256;
+  static constexpr int MINB = N1 >= 24 ? 3 : 4;
   static constexpr int LP = P + 1;
   static constexpr int SM_ELEMS = P + W * LP;
 };
