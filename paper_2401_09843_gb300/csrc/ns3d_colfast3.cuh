@@ -57,28 +57,30 @@ NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid
   const int c0 = bx * S::W;
   const int ncol = imin(S::W, a.ncols - c0);
   const cplx<T>* in = a.in + bz * a.in_bs + by * a.in_os + c0 * a.in_cs;
+#pragma unroll 1
   for (int t = tid; t < S::W * M; t += nthr) {
     const int col = t % S::W;
     const int jp = t / S::W;
     if (col >= ncol) continue;
     const cplx<T>* ic = in + col * a.in_cs;
+    const int rs = (int)a.in_rs;   // P rs < 2^31 (checked at dispatch)
     cplx<T> v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       const int p = M * j1 + jp;
       if (!PAD) {
-        v[j1] = ic[p * a.in_rs];
+        v[j1] = ic[p * rs];
       } else {
         const int reg = pad_region(M * j1, M, S::P, S::H);
         if (reg == PAD_ZERO) {
           v[j1] = czero<T>();
         } else if (reg == PAD_LOW) {
-          v[j1] = ic[p * a.in_rs];
+          v[j1] = ic[p * rs];
         } else if (reg == PAD_HIGH) {
-          v[j1] = ic[(p - S::H) * a.in_rs];          // row p - P + N
+          v[j1] = ic[(p - S::H) * rs];          // row p - P + N
         } else {
           const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
-          v[j1] = row >= 0 ? ic[row * a.in_rs] : czero<T>();
+          v[j1] = row >= 0 ? ic[row * rs] : czero<T>();
         }
       }
     }
@@ -92,6 +94,7 @@ NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid
 template <typename T, int SIGN, int N1, int N2, int N3>
 NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<T>* tw, cplx<T>* X) {
   using S = ColFast3Shape<N1, N2, N3>;
+#pragma unroll 1
   for (int t = tid; t < S::W * N1 * N3; t += nthr) {
     const int col = t % S::W;
     const int r = t / S::W;
@@ -116,6 +119,7 @@ NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid
   const int c0 = bx * S::W;
   const int ncol = imin(S::W, a.ncols - c0);
   cplx<T>* out = a.out + bz * a.out_bs + by * a.out_os + c0 * a.out_cs;
+#pragma unroll 1
   for (int t = tid; t < S::W * M; t += nthr) {
     const int col = t % S::W;
     const int r = t / S::W;
@@ -127,20 +131,21 @@ NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid
     for (int j3 = 0; j3 < N3; ++j3) v[j3] = D[j3 * N1];
     Dft<N3, SIGN>::run(v);
     cplx<T>* oc = out + col * a.out_cs;
+    const int rs = (int)a.out_rs;  // P rs < 2^31 (checked at dispatch)
 #pragma unroll
     for (int k3 = 0; k3 < N3; ++k3) {
       const int p = r + M * k3;
       if (!TRUNC) {
-        oc[p * a.out_rs] = a.scale * v[k3];
+        oc[p * rs] = a.scale * v[k3];
       } else {
         const int reg = pad_region(M * k3, M, S::P, S::H);
         if (reg == PAD_LOW) {
-          oc[p * a.out_rs] = a.scale * v[k3];
+          oc[p * rs] = a.scale * v[k3];
         } else if (reg == PAD_HIGH) {
-          oc[(p - S::H) * a.out_rs] = a.scale * v[k3];
+          oc[(p - S::H) * rs] = a.scale * v[k3];
         } else if (reg == PAD_MIXED) {
           const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
-          if (row >= 0) oc[row * a.out_rs] = a.scale * v[k3];
+          if (row >= 0) oc[row * rs] = a.scale * v[k3];
         }
       }
     }

@@ -46,7 +46,9 @@ template <typename T>
 cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaStream_t s) {
   const bool padded_inverse = kind == COL_INV_CC && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
   const bool truncated_forward = kind == COL_FWD_CC && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
-  if (sizeof(T) == 4 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
+  // the three-pass kernel indexes rows with 32-bit offsets
+  const bool rows32 = (long long)a.pl.n * (a.in_rs > a.out_rs ? a.in_rs : a.out_rs) < (1LL << 31);
+  if (sizeof(T) == 4 && 3 * a.h == a.pl.n && rows32 && (padded_inverse || truncated_forward)) {
     const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
 #define NS3D_CF3_GO(A, B, C)                                                        \
     if (a.pl.n == (A) * (B) * (C))                                                  \
