@@ -122,6 +122,17 @@ ns3d_status ns3d_set_initial(ns3d_plan plan, int member, const void* uhat, int u
 ns3d_status ns3d_get_state(ns3d_plan plan, int member, void* uhat_out, int out_on_device,
                            double* t_out);
 
+/* Member `member`'s clock: the time reached and the number of completed
+ * steps.  Synchronises; returns the member's sticky device status like
+ * ns3d_get_state. */
+ns3d_status ns3d_get_clock(ns3d_plan plan, int member, double* t, int* nsteps);
+
+/* Sets member `member`'s clock (t >= 0, nsteps >= 0), e.g. after
+ * ns3d_set_initial restored a checkpointed state: the run then continues
+ * exactly as if it had not stopped (the same steps, clipped at the same
+ * t_end).  Stream-ordered. */
+ns3d_status ns3d_set_clock(ns3d_plan plan, int member, double t, int nsteps);
+
 /* Advances every member by `nsteps` SSP-RK3 steps (eq. RK3; three evaluations
  * of Algorithm 2 each).  t_end > 0: a member's step is clipped so it stops at
  * t_end exactly, and members already at t_end do not move.  Asynchronous: the

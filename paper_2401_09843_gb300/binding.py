@@ -26,7 +26,8 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_set_initial", "ns3d_get_state", "ns3d_step", "ns3d_synchronize",
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
-           "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging"]
+           "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
+           "ns3d_set_clock"]
 
 
 class Ns3dError(RuntimeError):
@@ -79,6 +80,9 @@ def load(path: str = LIB_PATH):
         "ns3d_status_string": (ctypes.c_char_p, [i]),
         "ns3d_step_timed": (i, [vp, i, d, ctypes.POINTER(d), ip]),
         "ns3d_eval_rhs_noalloc": (i, [i, i, ctypes.POINTER(Params), vp, vp, vp]),
+        "ns3d_test_stall_staging": (i, [vp, i]),
+        "ns3d_get_clock": (i, [vp, i, ctypes.POINTER(d), ip]),
+        "ns3d_set_clock": (i, [vp, i, d, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -200,6 +204,16 @@ class Plan:
         _check(self.lib.ns3d_get_state(self.h, member, out.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(t)),
                "ns3d_get_state")
         return out, t.value
+
+    def clock(self, member: int):
+        """(t, completed steps) of a member; synchronises."""
+        t = ctypes.c_double()
+        n = ctypes.c_int()
+        _check(self.lib.ns3d_get_clock(self.h, member, ctypes.byref(t), ctypes.byref(n)), "ns3d_get_clock")
+        return t.value, n.value
+
+    def set_clock(self, member: int, t: float, nsteps: int):
+        _check(self.lib.ns3d_set_clock(self.h, member, ctypes.c_double(t), int(nsteps)), "ns3d_set_clock")
 
     def step(self, nsteps: int = 1, t_end: float = 0.0):
         _check(self.lib.ns3d_step(self.h, int(nsteps), float(t_end)), "ns3d_step")

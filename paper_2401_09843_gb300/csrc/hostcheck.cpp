@@ -275,6 +275,25 @@ void run_xfused(const XFusedArgs<T>& a) {
   }
 }
 
+template <typename T, int N1, int N2>
+void run_xfused_prologue(const XFusedArgs<T>& a) {
+  using S = XFusedShape<N1, N2>;
+  std::vector<cplx<T>> sm(2 * S::P + S::W * S::LP);
+  std::vector<cplx<T>> v((size_t)S::NTHR * N2);
+  const int ncols = a.N * a.h;
+  for (int bx = 0; bx < ncols / S::W; ++bx) {
+    for (int t = 0; t < S::NTHR; ++t) xfused_twiddles<T, N1, N2>(a, sm.data(), t, S::NTHR);
+    cplx<T>* X = sm.data() + 2 * S::P;
+    for (int q = 0; q < 3; ++q) {
+      for (int t = 0; t < S::NTHR; ++t) {
+        xfused_prologue_load<T, N1, N2>(a, bx, 0, q, t, &v[(size_t)t * N2]);
+        xfused_inv1<T, N1, N2>(t, sm.data(), X, &v[(size_t)t * N2]);
+      }
+      for (int t = 0; t < S::NTHR; ++t) xfused_inv2<T, N1, N2>(a, bx, 0, q, t, S::NTHR, X);
+    }
+  }
+}
+
 template <typename T>
 bool fused_shape(const ns3d::Geom& g) {
   if (!g_use_fast || sizeof(T) != 4 || 3 * g.h != g.P) return false;
@@ -379,8 +398,18 @@ int run(int N, int P, const double* prm, const void* uin, void* uout, int nsteps
     return 0;
   }
   if (fused_shape<T>(g)) {
-    run_col<T, +1, true, true>(ns3d::args_inv_x<T>(g, U0.data(), W1.data(), tw.data()),
-                               ns3d::launch_inv_x(g, 1), sm);
+    XFusedArgs<T> pa{};
+    pa.u0 = U0.data();
+    pa.ax = W1.data();
+    pa.tw = tw.data();
+    pa.N = g.N;
+    pa.h = g.h;
+    pa.m3 = g.nU;
+    pa.mA = g.nA;
+#define NS3D_HC_XP(A, B) \
+    if (g.P == (A) * (B)) run_xfused_prologue<T, A, B>(pa);
+    NS3D_FOR_XFUSED(NS3D_HC_XP)
+#undef NS3D_HC_XP
     for (int n = 0; n < nsteps; ++n) {
       fused_stage<T>(g, sp, U0.data(), US.data(), US.data(), 1, W1, W2, tw, &ctrl, sm);
       fused_stage<T>(g, sp, U0.data(), US.data(), US.data(), 2, W1, W2, tw, &ctrl, sm);

@@ -101,6 +101,45 @@ bail:
   }
 }
 
+// x-inverse of the stored state with the fused pass's own inverse phases
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR)
+    k_xfused_prologue(const XFusedArgs<T> a) {
+  using S = XFusedShape<N1, N2>;
+  extern __shared__ __align__(128) unsigned char ns3d_smem[];
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  cplx<T>* X = tw + 2 * S::P;
+  const int tid = threadIdx.x, bx = blockIdx.x, m = blockIdx.y;
+  xfused_twiddles<T, N1, N2>(a, tw, tid, S::NTHR);
+  __syncthreads();
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) {
+    {
+      cplx<T> v[N2];
+      xfused_prologue_load<T, N1, N2>(a, bx, m, q, tid, v);
+      xfused_inv1<T, N1, N2>(tid, tw, X, v);
+    }
+    __syncthreads();
+    xfused_inv2<T, N1, N2>(a, bx, m, q, tid, S::NTHR, X);
+    __syncthreads();
+  }
+}
+
+template <typename T, int N1, int N2>
+constexpr size_t xfused_prologue_smem() {
+  using S = XFusedShape<N1, N2>;
+  return (size_t)(2 * S::P + S::W * S::LP) * sizeof(cplx<T>);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t xfused_prologue_launch(const XFusedArgs<T>& a, int nm, cudaStream_t s) {
+  using S = XFusedShape<N1, N2>;
+  const int ncols = a.N * a.h;
+  if (ncols % S::W != 0 || 2 * S::H != a.N) return cudaErrorInvalidValue;
+  k_xfused_prologue<T, N1, N2><<<dim3(ncols / S::W, nm), S::NTHR, xfused_prologue_smem<T, N1, N2>(), s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int N1, int N2>
 constexpr size_t xfused_smem_bytes() {
   using S = XFusedShape<N1, N2>;
@@ -120,9 +159,13 @@ cudaError_t xfused_launch(const XFusedArgs<T>& a, const XFusedMaps& maps, int nm
 template <typename T, int N1, int N2>
 cudaError_t xfused_init() {
   static_assert(xfused_smem_bytes<T, N1, N2>() <= 227 * 1024, "fused x pass: shared memory");
-  return cudaFuncSetAttribute((const void*)k_xfused<T, N1, N2>,
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_xfused<T, N1, N2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)xfused_smem_bytes<T, N1, N2>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)k_xfused_prologue<T, N1, N2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)xfused_smem_bytes<T, N1, N2>());
+                              (int)xfused_prologue_smem<T, N1, N2>());
 }
 
 }  // namespace ns3d
@@ -132,4 +175,5 @@ cudaError_t xfused_init() {
   template cudaError_t xfused_launch<T, N1, N2>(const XFusedArgs<T>&, const XFusedMaps&, int, \
                                                 cudaStream_t);                             \
   template cudaError_t xfused_init<T, N1, N2>();                                           \
+  template cudaError_t xfused_prologue_launch<T, N1, N2>(const XFusedArgs<T>&, int, cudaStream_t); \
   }

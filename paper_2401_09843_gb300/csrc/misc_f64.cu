@@ -22,6 +22,13 @@ __global__ void k_ctrl_set_tend(Ns3dCtrl* c, int n, double t_end) {
   if (i < n) c[i].t_end = t_end;
 }
 
+__global__ void k_ctrl_set_clock(Ns3dCtrl* c, double t, int nsteps) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->t = t;
+    c->nsteps = nsteps;
+  }
+}
+
 __global__ void k_step_dt(Ns3dCtrl* c, int n, SpecParams sp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) step_dt_member(c[i], sp);
@@ -39,6 +46,11 @@ cudaError_t launch_ctrl_reset(Ns3dCtrl* c, int n, cudaStream_t s) {
 
 cudaError_t launch_ctrl_set_tend(Ns3dCtrl* c, int n, double t_end, cudaStream_t s) {
   k_ctrl_set_tend<<<(n + 127) / 128, 128, 0, s>>>(c, n, t_end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_set_clock(Ns3dCtrl* c, double t, int nsteps, cudaStream_t s) {
+  k_ctrl_set_clock<<<1, 32, 0, s>>>(c, t, nsteps);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,8 @@ bool xfused_make_maps(XFusedMaps* maps, const Geom& g, int B, const void* dq, co
 template <typename T, int N1, int N2>
 cudaError_t xfused_launch(const XFusedArgs<T>& a, const XFusedMaps& maps, int nm, cudaStream_t s);
 template <typename T, int N1, int N2>
+cudaError_t xfused_prologue_launch(const XFusedArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
 cudaError_t xfused_init();
 
 // The fused x pass exists for FP32 at P = N1 N2 with the default padding.
@@ -98,6 +100,16 @@ bool xfused_available(const Geom& g) {
   NS3D_FOR_XFUSED(NS3D_XF_CASE)
 #undef NS3D_XF_CASE
   return false;
+}
+
+template <typename T>
+cudaError_t launch_xfused_prologue(const XFusedArgs<T>& a, const Geom& g, int nm, cudaStream_t s) {
+  const XFusedArgs<float>& af = *reinterpret_cast<const XFusedArgs<float>*>(&a);
+#define NS3D_XFP_GO(A, B) \
+  if (g.P == (A) * (B)) return xfused_prologue_launch<float, A, B>(af, nm, s);
+  NS3D_FOR_XFUSED(NS3D_XFP_GO)
+#undef NS3D_XFP_GO
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -197,5 +209,6 @@ cudaError_t kernels_init() {
 
 cudaError_t launch_ctrl_reset(Ns3dCtrl* c, int n, cudaStream_t s);
 cudaError_t launch_ctrl_set_tend(Ns3dCtrl* c, int n, double t_end, cudaStream_t s);
+cudaError_t launch_ctrl_set_clock(Ns3dCtrl* c, double t, int nsteps, cudaStream_t s);
 
 }  // namespace ns3d

@@ -292,6 +292,29 @@ NS3D_HD void xfused_combine(const XFusedArgs<T>& a, int bx, int m, int q, int ti
   }
 }
 
+// Prologue (the x-inverse of a state set outside a step): the stored state
+// of component q at the thread's positions, exactly the values the combine
+// leaves in v for a member that does not move, so that xfused_inv1/2 on them
+// give A bit for bit as the fused pass would
+template <typename T, int N1, int N2>
+NS3D_HD void xfused_prologue_load(const XFusedArgs<T>& a, int bx, int m, int q, int tid,
+                                  cplx<T>* v) {
+  using S = XFusedShape<N1, N2>;
+  const int col = tid % S::W, k1 = tid / S::W;
+  const int h = a.h, N = a.N;
+  const int ncols = N * h;
+  const int c = bx * S::W + col;
+  const bool nyq = (c / h) % N == h;
+  const cplx<T>* u = a.u0 + m * a.m3 + (long long)q * N * ncols + c;
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const int sx = xf_freq<S::P, S::H>(k1 + N1 * k2);
+    cplx<T> nv = czero<T>();
+    if (sx > -h && sx < h && !nyq) nv = u[(long long)(sx < 0 ? sx + N : sx) * ncols];
+    v[k2] = nv;
+  }
+}
+
 // the thread holding k = 0 of the member advances its clock after stage 3
 // (the other threads of this launch read only dt)
 template <typename T, int N1, int N2>

@@ -191,12 +191,19 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
 
 // x-inverse of every member's state into W1 (needed before the first fused
 // stage after the state or W1 changed outside a step)
+// (with the fused pass's own inverse phases, so that a state set from a
+// checkpoint continues bit for bit as if the run had not stopped)
 template <typename T>
 ns3d_status enqueue_prologue(Level& L, cudaStream_t s) {
-  const cplx<T>* U0 = static_cast<const cplx<T>*>(L.U0);
-  NS3D_CK(launch_col<T>(args_inv_x<T>(L.g, U0, static_cast<cplx<T>*>(L.W1),
-                                      static_cast<const cplx<T>*>(L.twP)),
-                        COL_INV_CC, launch_inv_x(L.g, L.B), s));
+  XFusedArgs<T> x{};
+  x.u0 = static_cast<const cplx<T>*>(L.U0);
+  x.ax = static_cast<cplx<T>*>(L.W1);
+  x.tw = static_cast<const cplx<T>*>(L.twP);
+  x.N = L.g.N;
+  x.h = L.g.h;
+  x.m3 = L.g.nU;
+  x.mA = L.g.nA;
+  NS3D_CK(launch_xfused_prologue<T>(x, L.g, L.B, s));
   L.a_valid = true;
   return NS3D_OK;
 }
@@ -525,6 +532,32 @@ extern "C" ns3d_status ns3d_get_state(ns3d_plan p, int member, void* out, int on
   NS3D_CK(cudaStreamSynchronize(p->stream));
   if (t_out) *t_out = c.t;
   return status_of_flags(c.status);
+}
+
+extern "C" ns3d_status ns3d_get_clock(ns3d_plan p, int member, double* t, int* nsteps) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (!t || !nsteps) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  Ns3dCtrl c;
+  NS3D_CK(cudaMemcpyAsync(&c, L->ctrl + idx, sizeof(c), cudaMemcpyDeviceToHost, p->stream));
+  NS3D_CK(cudaStreamSynchronize(p->stream));
+  *t = c.t;
+  *nsteps = c.nsteps;
+  return status_of_flags(c.status);
+}
+
+extern "C" ns3d_status ns3d_set_clock(ns3d_plan p, int member, double t, int nsteps) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  if (!(t >= 0.0) || nsteps < 0) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  NS3D_CK(launch_ctrl_set_clock(L->ctrl + idx, t, nsteps, p->stream));
+  return NS3D_OK;
 }
 
 extern "C" ns3d_status ns3d_step(ns3d_plan p, int nsteps, double t_end) {
