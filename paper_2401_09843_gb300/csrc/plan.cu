@@ -16,6 +16,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ns3d.h"
 #include "ns3d_launch.h"
 #include "plan_internal.h"
@@ -52,6 +54,12 @@ struct DeviceGuard {
     int cur = -1;
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
+};
+
+// NVTX range over one C-ABI call (visible in Nsight Systems timelines)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
 };
 
 }  // namespace
@@ -161,8 +169,16 @@ size_t lambda_entries(const Geom& g) { return 3 * (size_t)(g.h - 1) * (g.h - 1) 
 // One evaluation of Algorithm 2 plus the spectral step for members
 // [m0, m0 + nm) of a level.  `in` is the field R is evaluated at; stage 0
 // writes R to `out`, stages 1-3 the SSP-RK3 combinations.
-#define NS3D_MARK(i) \
-  if (tm) NS3D_CK(cudaEventRecord(tm->ev[i], s))
+// kernel kinds of one stage, for CUDA events and NVTX ranges (eager timing)
+const char* const kKindNames[6] = {"inverse x", "inverse y", "z pass", "forward y", "forward x",
+                                   "spectral / fused x"};
+
+#define NS3D_MARK(i)                                      \
+  if (tm) {                                               \
+    NS3D_CK(cudaEventRecord(tm->ev[i], s));               \
+    if ((i) > 0) nvtxRangePop();                          \
+    if ((i) < 6) nvtxRangePushA(kKindNames[(i) < 6 ? (i) : 0]); \
+  }
 
 StageBufs level_bufs(Level& L, int m0) {
   StageBufs b;
@@ -561,6 +577,7 @@ extern "C" ns3d_status ns3d_set_clock(ns3d_plan p, int member, double t, int nst
 }
 
 extern "C" ns3d_status ns3d_step(ns3d_plan p, int nsteps, double t_end) {
+  NvtxRange nvtx_("ns3d_step");
   if (!p || nsteps < 0) return NS3D_ERR_INVALID_ARG;
   if (nsteps == 0) return NS3D_OK;
   DeviceGuard dg(p->device);
@@ -591,6 +608,7 @@ extern "C" ns3d_status ns3d_synchronize(ns3d_plan p) {
 
 extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, void* rhs,
                                      int on_device) {
+  NvtxRange nvtx_("ns3d_eval_rhs");
   Level* L;
   int idx;
   ns3d_status st = member_lookup(p, member, &L, &idx);
@@ -633,6 +651,7 @@ extern "C" ns3d_status ns3d_test_stall_staging(ns3d_plan p, int on) {
 
 extern "C" ns3d_status ns3d_step_timed(ns3d_plan p, int nsteps, double t_end, double* kernel_ms,
                                        int* launches) {
+  NvtxRange nvtx_("ns3d_step_timed");
   if (!p || nsteps < 0 || !kernel_ms || !launches) return NS3D_ERR_INVALID_ARG;
   DeviceGuard dg(p->device);
   if (t_end != p->t_end) {
