@@ -241,6 +241,13 @@ ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d_params* p,
  * default. */
 ns3d_status ns3d_test_stall_staging(ns3d_plan plan, int on);
 
+/* Test hook (no counterpart in the paper): fills every level's workspaces and
+ * stage-state buffer with all-ones bytes, a NaN in FP32 and FP64, so that a
+ * kernel that reads a workspace element no earlier pass wrote shows up as a
+ * NONFINITE status or a wrong result.  The state itself is left alone; the
+ * next step re-derives everything it needs from it.  Stream-ordered. */
+ns3d_status ns3d_test_poison_workspaces(ns3d_plan plan);
+
 const char* ns3d_status_string(ns3d_status s);
 
 #ifdef __cplusplus

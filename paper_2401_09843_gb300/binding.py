@@ -27,7 +27,7 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
            "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
-           "ns3d_set_clock"]
+           "ns3d_set_clock", "ns3d_test_poison_workspaces"]
 
 
 class Ns3dError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "ns3d_test_stall_staging": (i, [vp, i]),
         "ns3d_get_clock": (i, [vp, i, ctypes.POINTER(d), ip]),
         "ns3d_set_clock": (i, [vp, i, d, i]),
+        "ns3d_test_poison_workspaces": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +205,10 @@ class Plan:
         _check(self.lib.ns3d_get_state(self.h, member, out.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(t)),
                "ns3d_get_state")
         return out, t.value
+
+    def test_poison_workspaces(self):
+        """Test hook: NaN-fill the workspaces and stage buffer (see ns3d.h)."""
+        _check(self.lib.ns3d_test_poison_workspaces(self.h), "ns3d_test_poison_workspaces")
 
     def clock(self, member: int):
         """(t, completed steps) of a member; synchronises."""

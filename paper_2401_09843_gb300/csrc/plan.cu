@@ -631,6 +631,19 @@ extern "C" ns3d_status ns3d_eval_rhs(ns3d_plan p, int member, const void* uhat, 
   return NS3D_OK;
 }
 
+extern "C" ns3d_status ns3d_test_poison_workspaces(ns3d_plan p) {
+  if (!p) return NS3D_ERR_INVALID_ARG;
+  DeviceGuard dg(p->device);
+  for (Level& L : p->levels) {
+    const Geom& g = L.g;
+    NS3D_CK(cudaMemsetAsync(L.W1, 0xFF, (size_t)L.B * g.nW1 * p->esz, p->stream));
+    NS3D_CK(cudaMemsetAsync(L.W2, 0xFF, (size_t)L.B * g.nW2 * p->esz, p->stream));
+    NS3D_CK(cudaMemsetAsync(L.US, 0xFF, (size_t)L.B * g.nU * p->esz, p->stream));
+    L.a_valid = false;   // W1 no longer holds the x-inverse of the state
+  }
+  return NS3D_OK;
+}
+
 extern "C" ns3d_status ns3d_test_stall_staging(ns3d_plan p, int on) {
   if (!p) return NS3D_ERR_INVALID_ARG;
   bool any = false;

@@ -3,7 +3,8 @@ FP64, P = 1152) through the C ABI, in the launch shapes the plan uses there
 (arrays of up to 7e9 complex elements per member: 64-bit offsets throughout).
 
 The inputs are built on the device from mode lists, so the host never holds
-a dense field of these sizes: a sparse random field against the oracle's
+a dense field of these sizes (and the workspaces are NaN-filled first, so a
+read of an element no pass wrote would show): a sparse random field against the oracle's
 mode-pair Galerkin sum (rhs_sparse), and an ABC Beltrami field whose
 projected nonlinear term vanishes, so that n fixed-dt RK3 steps multiply it
 by r(-lambda_K dt)^n exactly (r the RK3 stability polynomial)."""
@@ -48,6 +49,7 @@ def test_rhs_largest_grids_sparse_field(B, N, dt):
     assert np.max(np.abs(K[:, :2])) > N // 2 - 64     # modes near the band edge
     Ko, Rref = S.rhs_sparse(K, V, N, prm)
     p = B.Plan([N], dtype, nu=0.0, eps0=1.0)
+    p.test_poison_workspaces()          # every workspace read must have been written
     u, _ = on_device(torch, K, V, N, cdt)
     R = p.eval_rhs(0, u)
     p.synchronize()
@@ -81,6 +83,7 @@ def test_beltrami_steps_largest_grids(B, N, dt, nsteps):
     assert lam * prm.dt_fixed > 0.01
     r = S.rk3_amplification(-lam * prm.dt_fixed) ** nsteps
     p = B.Plan([N], dtype, nu=0.0, eps0=1.0, dt_fixed=2e-3)
+    p.test_poison_workspaces()          # every workspace read must have been written
     u, (ix, iy, iz) = on_device(torch, K, V, N, cdt)
     p.set_initial(0, u)
     p.step(nsteps)
