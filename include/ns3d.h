@@ -67,8 +67,14 @@ typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
  *   eps_N = eps0 * N^(1-2s),  m_N = mN_coef * N^theta
  *   Q_k = 0 for |k| <= m_N, else 1 - (m_N/|k|)^((2s-1)/theta) (q_form 0) or 1 (q_form 1)
  *   (|k| the integer wavenumber; the paper's "+eps_N" is read as damping).
- *   n_pad: padded FFT size P (0: smallest 2^a 3^b 5^c 7^d >= 3N/2, section 3.1;
- *          values below 3N/2 alias and are rejected).
+ *   n_pad: padded FFT size P.  0: chosen at plan creation (section 3.1): the
+ *          smallest 2^a 3^b 5^c 7^d >= 3N/2 where the register kernels exist
+ *          (FP32, P = 3N/2 in {48, 96, 192, 384, 1536}), otherwise the fastest
+ *          of the 7-smooth sizes up to 12.5% above it by a timed right-hand
+ *          side (cached per device, N and dtype; also in the file named by the
+ *          environment variable NS3D_AUTOTUNE_CACHE, if set).  -1: the
+ *          smallest such size without a benchmark.  > 0: that size (values
+ *          below 3N/2 alias and are rejected).
  *   nonlinear_form: 0 = divergence form -i k.F[u (x) u] (the paper's; the only
  *          one the GPU path implements; 1 and 2 return NS3D_ERR_NOT_SUPPORTED).
  *   dt_fixed > 0: fixed time step; otherwise dt = cfl * (L/N) / max_x sum_i |u_i|

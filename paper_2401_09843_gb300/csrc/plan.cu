@@ -11,8 +11,13 @@
 //   -> forward y (truncate) -> forward x (truncate) -> spectral step + combine,
 // i.e. Algorithm 2 with the padding fused into the transforms (Algorithm 3).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -384,6 +389,121 @@ ns3d_status status_of_flags(int flags) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------- autotune
+// The padded size (section 3.1): the smallest 2^a 3^b 5^c 7^d >= 3N/2 unless
+// a benchmark of a few larger candidates says otherwise.  Where the register
+// kernels exist (FP32 at P = 3N/2) the smallest size is taken without one.
+
+bool register_kernels_at(int N, int P, ns3d_dtype dtype) {
+  if (dtype != NS3D_F32 || 2 * P != 3 * N) return false;
+  return zfast_available<float>(P) || zfast3_available<float>(P);
+}
+
+std::vector<int> pad_candidates(int N) {
+  std::vector<int> c;
+  const int P0 = default_padded_size(N);
+  for (int P = P0; P <= P0 + P0 / 8 && c.size() < 4; ++P)
+    if (is_7_smooth(P)) c.push_back(P);
+  return c;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<std::string, int, int>, int> g_tune;   // (device, N, dtype) -> P
+bool g_tune_loaded = false;
+
+// optional cache file (environment NS3D_AUTOTUNE_CACHE): lines "device<TAB>N dtype P"
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("NS3D_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    char* tab = std::strchr(line, '\t');
+    if (!tab) continue;
+    int N = 0, dt = 0, P = 0;
+    if (std::sscanf(tab + 1, "%d %d %d", &N, &dt, &P) == 3 && 2 * P >= 3 * N)
+      g_tune[std::make_tuple(std::string(line, tab), N, dt)] = P;
+  }
+  std::fclose(f);
+}
+
+void tune_cache_store(const std::string& dev, int N, int dt, int P) {
+  const char* path = std::getenv("NS3D_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s\t%d %d %d\n", dev.c_str(), N, dt, P);
+  std::fclose(f);
+}
+
+// milliseconds of one right-hand side at (N, P) through the public entry
+// points, best of three after a warm-up; negative if the size cannot be run
+double time_rhs(int N, int P, ns3d_dtype dtype, ns3d_params prm, cudaStream_t s) {
+  prm.n_pad = P;
+  ns3d_plan tp = nullptr;
+  if (ns3d_plan_create(&tp, &N, 1, dtype, &prm, s, 0) != NS3D_OK) return -1.0;
+  const size_t bytes = d1_bytes(N, dtype == NS3D_F32 ? 8 : 16);
+  void* in = nullptr;
+  void* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best = -1.0;
+  if (cudaMalloc(&in, bytes) == cudaSuccess && cudaMalloc(&out, bytes) == cudaSuccess &&
+      cudaMemsetAsync(in, 0, bytes, s) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+      cudaEventCreate(&e1) == cudaSuccess && ns3d_eval_rhs(tp, 0, in, out, 1) == NS3D_OK) {
+    for (int r = 0; r < 3; ++r) {
+      float ms = 0.f;
+      if (cudaEventRecord(e0, s) != cudaSuccess || ns3d_eval_rhs(tp, 0, in, out, 1) != NS3D_OK ||
+          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        best = -1.0;
+        break;
+      }
+      if (best < 0 || ms < best) best = ms;
+    }
+  }
+  cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (in) cudaFree(in);
+  if (out) cudaFree(out);
+  ns3d_plan_destroy(tp);
+  return best;
+}
+
+int autotune_padded_size(int N, ns3d_dtype dtype, const ns3d_params& prm, cudaStream_t s) {
+  const std::vector<int> cand = pad_candidates(N);
+  if (cand.size() < 2 || register_kernels_at(N, cand[0], dtype)) return cand[0];
+  int dev = 0;
+  cudaDeviceProp pr{};
+  std::string name = "unknown";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&pr, dev) == cudaSuccess)
+    name = pr.name;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_cache_load();
+  const auto key = std::make_tuple(name, N, (int)dtype);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) return it->second;
+  int bestP = cand[0];
+  double bestT = -1.0;
+  for (int P : cand) {
+    const double t = time_rhs(N, P, dtype, prm, s);
+    if (t > 0 && (bestT < 0 || t < bestT)) {
+      bestT = t;
+      bestP = P;
+    }
+  }
+  g_tune[key] = bestP;
+  tune_cache_store(name, N, (int)dtype, bestP);
+  return bestP;
+}
+
+}  // namespace
+
 extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member, int batch,
                                         ns3d_dtype dtype, const ns3d_params* prm,
                                         void* cuda_stream, size_t workspace_limit_bytes) {
@@ -395,7 +515,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
   if (prm) P = *prm;
   else ns3d_params_default(&P);
   if (!(P.L > 0) || !(P.nu >= 0) || !(P.s >= 0.5) || !(P.theta > 0) || !(P.eps0 >= 0) ||
-      !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < 0 ||
+      !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < -1 ||
       !(P.dt_fixed >= 0) || (P.dt_fixed == 0 && !(P.cfl > 0)))
     return NS3D_ERR_INVALID_ARG;
   if (P.nonlinear_form != 0) return NS3D_ERR_NOT_SUPPORTED;
@@ -418,9 +538,13 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     L.N = kv.first;
     L.B = (int)kv.second.size();
     L.members = kv.second;
-    if (P.n_pad) {
+    if (P.n_pad > 0) {
       if (2 * P.n_pad < 3 * L.N) { delete p; return NS3D_ERR_INVALID_ARG; }
       L.P = P.n_pad;
+    } else if (P.n_pad == 0) {
+      if (dtype == NS3D_F32) kernels_init<float>();
+      else kernels_init<double>();
+      L.P = autotune_padded_size(L.N, dtype, P, p->stream);
     } else {
       L.P = default_padded_size(L.N);
     }

@@ -141,7 +141,7 @@ def test_random_ic_cfl_steps(B, dt):
     p.set_initial(0, u0)
     p.step(5)
     got, t = p.get_state(0, with_time=True)
-    ref, tref, _ = S.integrate(u0, prm, 5)
+    ref, tref, _ = S.integrate(u0, prm, 5, P=p.info(0)["P"])   # the CFL max is taken on the padded grid
     assert abs(t - tref) < (1e-13 if dt == "f64" else 1e-6) * tref
     assert rel(got.cpu().numpy(), ref) < (TOL64 if dt == "f64" else TOL32)
     p.close()
@@ -159,7 +159,7 @@ def test_uneven_batch_matches_individual_runs(B):
     p.step(3)
     for m, n in enumerate(Ns):
         got, t = p.get_state(m, with_time=True)
-        ref, tref, _ = S.integrate(u0[m], prm, 3)
+        ref, tref, _ = S.integrate(u0[m], prm, 3, P=p.info(m)["P"])
         assert abs(t - tref) < 1e-13
         assert rel(got.cpu().numpy(), ref) < TOL64, m
     p.close()
@@ -176,7 +176,7 @@ def test_t_end_clipping_and_frozen_members(B):
     for m, scale in ((0, 1.0), (1, 0.5)):
         got, t = p.get_state(m, with_time=True)
         assert abs(t - 0.25) < 1e-14
-        ref, tref, _ = S.integrate(scale * u0, prm, 60, t_end=0.25)
+        ref, tref, _ = S.integrate(scale * u0, prm, 60, t_end=0.25, P=p.info(m)["P"])
         assert abs(tref - 0.25) < 1e-14
         assert rel(got.cpu().numpy(), ref) < TOL64
     before = p.get_state(0).cpu().numpy()
@@ -322,3 +322,45 @@ def test_no_kernel_reads_unwritten_workspace(B, N, dt):
     if N <= 64:
         ref, _, _ = S.integrate(u0, prm, 2)
         assert rel(s1, ref) < (TOL64 if dt == "f64" else TOL32)
+
+
+def test_padded_size_autotune(B):
+    """n_pad = 0 times a right-hand side at the 7-smooth sizes within 12.5% of
+    3N/2 where no register kernel exists and keeps the fastest; the result is
+    the same Galerkin truncation (matches the oracle).  Register-kernel sizes
+    and n_pad = -1 take the smallest size."""
+    N = 24
+    uh = I.random_spectrum(N, seed=5, k0=3.0)
+    prm = S.Params(eps0=1.0)
+    p = plan(B, [N], B.NS3D_F64, eps0=1.0)
+    assert p.info(0)["P"] in (36, 40)
+    assert rel(p.eval_rhs(0, uh).cpu().numpy(), S.rhs(uh, prm)) < TOL64
+    p.close()
+    p = plan(B, [N], B.NS3D_F64, eps0=1.0, n_pad=-1)
+    assert p.info(0)["P"] == 36
+    p.close()
+    p = plan(B, [64], B.NS3D_F32, eps0=1.0)
+    assert p.info(0)["P"] == 96
+    p.close()
+
+
+def test_autotune_cache_file(tmp_path):
+    """The autotune result is appended to NS3D_AUTOTUNE_CACHE and read back
+    by the next process."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2401_09843_gb300 import binding as B\n"
+            "p = B.Plan([26], B.NS3D_F64, eps0=1.0)\n"
+            "print(p.info(0)['P'])\n" % root)
+    env = dict(os.environ, NS3D_AUTOTUNE_CACHE=str(cache))
+    P1 = int(subprocess.run([sys.executable, "-c", code], env=env, check=True,
+                            stdout=subprocess.PIPE, text=True).stdout.split()[-1])
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].split("\t")[1].split() == ["26", "1", str(P1)]
+    P2 = int(subprocess.run([sys.executable, "-c", code], env=env, check=True,
+                            stdout=subprocess.PIPE, text=True).stdout.split()[-1])
+    assert P2 == P1 and len(cache.read_text().splitlines()) == 1
