@@ -187,7 +187,15 @@ ns3d_status ns3d_grad_band_energy(ns3d_plan plan, int member, double k_lo, doubl
  *   s2, s2_se     [N/2]         mean and standard error of
  *                               S2(r) = (1/3) sum_d <|u(x + r e_d) - u(x)|^2>, r = jL/N
  *   energy, energy_se           mean and standard error of E = 1/2 <|u|^2>
- *   members                     M, the number of members of the level */
+ *   members                     M, the number of members of the level
+ *   enstrophy_spectrum[_se] [N] mean and standard error of
+ *                               Z(K) = 1/2 sum_{round|k| = K} |kappa|^2 |u_hat_k|^2
+ *                               (= 1/2 |omega_hat|^2 by shell for divergence-free u)
+ *   enstrophy, enstrophy_se     of Z = 1/2 <|omega|^2> = sum_K Z(K)
+ *   dissipation, dissipation_se of D = sum_k lambda_k |u_hat_k|^2 over the full
+ *                               spectrum: the exact energy loss rate -dE/dt of
+ *                               the semi-discrete system (the dealiased
+ *                               nonlinear term conserves E) */
 typedef struct {
   double* mean;
   double* second;
@@ -199,9 +207,22 @@ typedef struct {
   double energy;
   double energy_se;
   int members;
+  double* enstrophy_spectrum;
+  double* enstrophy_spectrum_se;
+  double enstrophy;
+  double enstrophy_se;
+  double dissipation;
+  double dissipation_se;
 } ns3d_stats;
 
 ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);
+
+/* |omega(x)|, the vorticity magnitude of member `member` at the N^3 grid points
+ * x_j = j L/N (omega = curl u, from omega_hat = i kappa x u_hat; the paper's
+ * vorticity field, section 6.1), as a real array [N][N][N] (z fastest) of the
+ * plan dtype in device or host memory per out_on_device.  Synchronises.
+ * NOT_SUPPORTED if N has a prime factor above 7. */
+ns3d_status ns3d_vorticity_magnitude(ns3d_plan plan, int member, void* out, int out_on_device);
 
 /* Diagnostic: advances every member by `nsteps` steps like ns3d_step, but
  * launches the kernels one by one (no graph) with CUDA events recorded on the

@@ -16,6 +16,13 @@ formulas for them; the definitions used (both here and in the library) are:
 * structure function    S2(r)     = (1/3) sum_d <|u(x + r e_d) - u(x)|^2>_x
                                   = (1/3) sum_d sum_k 2 |u_hat_k|^2 (1 - cos(kappa_d r)),
                         r = j L / N, j = 1 .. N/2
+* enstrophy spectrum    Z(K)      = 1/2 sum_{k : round(|k|) = K} |omega_hat_k|^2,
+                        omega_hat = i kappa x u_hat (the vorticity the paper's
+                        section 6.1 shows, as a spectrum writer)
+* dissipation rate      D         = sum_k lambda_k |u_hat_k|^2 (full spectrum):
+                        -dE/dt of the spectral equation (section 2.3), whose
+                        dealiased nonlinear term conserves energy
+* vorticity magnitude   |omega(x)| on the N^3 grid
 * Monte Carlo standard error of a sample mean: sqrt(var / M).
 
 Sample sets are merged with the pairwise formula of Chan, Golub and LeVeque
@@ -27,7 +34,7 @@ import math
 
 import numpy as np
 
-from .solver import half_weights, to_physical, wavenumbers
+from .solver import curl, dissipation, half_weights, to_physical, wavenumbers
 
 PAIRS = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
 
@@ -78,6 +85,25 @@ def structure_function_brute(u: np.ndarray) -> np.ndarray:
     return out
 
 
+def enstrophy_spectrum(uhat: np.ndarray, L: float) -> np.ndarray:
+    """Z(K) = 1/2 sum over round(|k|) = K of |omega_hat_k|^2, full spectrum;
+    the vorticity from its definition omega_hat = i kappa x u_hat."""
+    return energy_spectrum(curl(uhat, L))
+
+
+def dissipation_rate(uhat: np.ndarray, prm) -> float:
+    """D = sum_k lambda_k |u_hat_k|^2 over the full spectrum."""
+    N = uhat.shape[-2]
+    w = half_weights(N)
+    return float(np.sum(w * dissipation(N, prm) * np.sum(np.abs(uhat) ** 2, axis=0)))
+
+
+def vorticity_magnitude(uhat: np.ndarray, L: float) -> np.ndarray:
+    """|omega(x)| at the N^3 grid points."""
+    w = physical_on_grid(curl(uhat, L))
+    return np.sqrt(np.sum(w * w, axis=0))
+
+
 def mean_and_stderr(samples: np.ndarray):
     """Sample mean and Monte Carlo standard error along axis 0."""
     M = samples.shape[0]
@@ -88,8 +114,9 @@ def mean_and_stderr(samples: np.ndarray):
     return mean, np.sqrt(var / M)
 
 
-def ensemble_stats(uhats: np.ndarray, L: float) -> dict:
-    """All writer statistics of an ensemble given as (M, 3, N, N, N/2+1)."""
+def ensemble_stats(uhats: np.ndarray, L: float, prm=None) -> dict:
+    """All writer statistics of an ensemble given as (M, 3, N, N, N/2+1);
+    the dissipation rate needs the solver parameters prm."""
     M = uhats.shape[0]
     N = uhats.shape[-2]
     phys = np.stack([physical_on_grid(u) for u in uhats])           # (M,3,N,N,N)
@@ -102,10 +129,19 @@ def ensemble_stats(uhats: np.ndarray, L: float) -> dict:
     spec_m, spec_se = mean_and_stderr(spec)
     s2_m, s2_se = mean_and_stderr(s2)
     en_m, en_se = mean_and_stderr(en)
-    return dict(M=M, N=N, mean=mean, second=second, var=var,
-                spectrum=spec_m, spectrum_stderr=spec_se,
-                s2=s2_m, s2_stderr=s2_se,
-                energy=float(en_m), energy_stderr=float(en_se))
+    zspec = np.stack([enstrophy_spectrum(u, L) for u in uhats])
+    zs_m, zs_se = mean_and_stderr(zspec)
+    z_m, z_se = mean_and_stderr(zspec.sum(axis=1))
+    out = dict(M=M, N=N, mean=mean, second=second, var=var,
+               spectrum=spec_m, spectrum_stderr=spec_se,
+               s2=s2_m, s2_stderr=s2_se,
+               energy=float(en_m), energy_stderr=float(en_se),
+               enstrophy_spectrum=zs_m, enstrophy_spectrum_stderr=zs_se,
+               enstrophy=float(z_m), enstrophy_stderr=float(z_se))
+    if prm is not None:
+        d_m, d_se = mean_and_stderr(np.array([dissipation_rate(u, prm) for u in uhats]))
+        out.update(dissipation=float(d_m), dissipation_stderr=float(d_se))
+    return out
 
 
 def chan_merge(a, b):

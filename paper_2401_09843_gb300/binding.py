@@ -27,7 +27,7 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
            "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
-           "ns3d_set_clock", "ns3d_test_poison_workspaces"]
+           "ns3d_set_clock", "ns3d_test_poison_workspaces", "ns3d_vorticity_magnitude"]
 
 
 class Ns3dError(RuntimeError):
@@ -49,7 +49,10 @@ class Stats(ctypes.Structure):
                 ("spectrum", ctypes.c_void_p), ("spectrum_se", ctypes.c_void_p),
                 ("s2", ctypes.c_void_p), ("s2_se", ctypes.c_void_p),
                 ("energy", ctypes.c_double), ("energy_se", ctypes.c_double),
-                ("members", ctypes.c_int)]
+                ("members", ctypes.c_int),
+                ("enstrophy_spectrum", ctypes.c_void_p), ("enstrophy_spectrum_se", ctypes.c_void_p),
+                ("enstrophy", ctypes.c_double), ("enstrophy_se", ctypes.c_double),
+                ("dissipation", ctypes.c_double), ("dissipation_se", ctypes.c_double)]
 
 
 _lib = None
@@ -84,6 +87,7 @@ def load(path: str = LIB_PATH):
         "ns3d_get_clock": (i, [vp, i, ctypes.POINTER(d), ip]),
         "ns3d_set_clock": (i, [vp, i, d, i]),
         "ns3d_test_poison_workspaces": (i, [vp]),
+        "ns3d_vorticity_magnitude": (i, [vp, i, vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -277,12 +281,23 @@ class Plan:
         arrays["spectrum_se"] = np.zeros(N)
         arrays["s2"] = np.zeros(N // 2)
         arrays["s2_se"] = np.zeros(N // 2)
+        arrays["enstrophy_spectrum"] = np.zeros(N)
+        arrays["enstrophy_spectrum_se"] = np.zeros(N)
         st = Stats()
         for k, v in arrays.items():
             setattr(st, k, v.ctypes.data_as(ctypes.c_void_p))
         _check(self.lib.ns3d_ensemble_stats(self.h, N, ctypes.byref(st)), "ns3d_ensemble_stats")
         res.update(arrays)
-        res["energy"] = st.energy
-        res["energy_se"] = st.energy_se
+        for k in ("energy", "energy_se", "enstrophy", "enstrophy_se", "dissipation", "dissipation_se"):
+            res[k] = getattr(st, k)
         res["members"] = st.members
         return res
+
+    def vorticity_magnitude(self, member: int):
+        """|omega(x)| on the member's N^3 grid: a CUDA tensor [N][N][N]."""
+        n = self.N[member]
+        rdt = self.torch.float32 if self.dtype == NS3D_F32 else self.torch.float64
+        out = self.torch.empty((n, n, n), dtype=rdt, device="cuda")
+        _check(self.lib.ns3d_vorticity_magnitude(self.h, member, ctypes.c_void_p(out.data_ptr()), 1),
+               "ns3d_vorticity_magnitude")
+        return out

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-_PAIRS = ["spectrum", "s2", "energy"]
+_PAIRS = ["spectrum", "s2", "energy", "enstrophy_spectrum", "enstrophy", "dissipation"]
 
 
 def _m2_from_se(se, n):
@@ -39,6 +39,8 @@ def merge_stats(a: dict, b: dict) -> dict:
     n = na + nb
     out = {"members": n}
     for key in _PAIRS:
+        if key not in a or key not in b:
+            continue
         se_key = key + "_se"
         ma, mb = np.asarray(a[key], dtype=np.float64), np.asarray(b[key], dtype=np.float64)
         d = mb - ma

@@ -11,15 +11,21 @@ from paper_2401_09843_gb300.ensemble import merge_stats
 pytestmark = pytest.mark.gpu
 
 KEYS = [("mean", "mean"), ("second", "second"), ("var", "var"), ("spectrum", "spectrum"),
-        ("spectrum_se", "spectrum_stderr"), ("s2", "s2"), ("s2_se", "s2_stderr")]
+        ("spectrum_se", "spectrum_stderr"), ("s2", "s2"), ("s2_se", "s2_stderr"),
+        ("enstrophy_spectrum", "enstrophy_spectrum"),
+        ("enstrophy_spectrum_se", "enstrophy_spectrum_stderr")]
+SCALARS = ["energy", "enstrophy", "dissipation"]
 
 
 def _check(gpu, ref, rtol):
     for gk, rk in KEYS:
         a, b = np.asarray(gpu[gk]), np.asarray(ref[rk])
         assert np.max(np.abs(a - b)) <= rtol * max(np.max(np.abs(b)), 1e-30), gk
-    assert abs(gpu["energy"] - ref["energy"]) <= rtol * ref["energy"]
-    assert abs(gpu["energy_se"] - ref["energy_stderr"]) <= rtol * max(ref["energy"], 1e-30)
+    for k in SCALARS:
+        if k not in ref:
+            continue
+        assert abs(gpu[k] - ref[k]) <= rtol * ref[k], k
+        assert abs(gpu[k + "_se"] - ref[k + "_stderr"]) <= rtol * max(ref[k], 1e-30), k
     assert gpu["members"] == ref["M"]
 
 
@@ -28,14 +34,54 @@ def test_stats_match_oracle(lib, dt, rtol):
     from paper_2401_09843_gb300 import binding as B
     dtype = B.NS3D_F64 if dt == "f64" else B.NS3D_F32
     Ns = [16, 8, 16, 16, 8, 16, 16]          # two levels; the N = 16 level has 5 members
-    p = B.Plan(Ns, dtype, eps0=1.0)
+    p = B.Plan(Ns, dtype, eps0=1.0, nu=0.01)
+    prm = S.Params(eps0=1.0, nu=0.01)
     u = [I.random_spectrum(n, seed=41, member=m, k0=2.5) for m, n in enumerate(Ns)]
     for m, x in enumerate(u):
         p.set_initial(m, x)
     for N in (16, 8):
         mem = [m for m, n in enumerate(Ns) if n == N]
-        ref = T.ensemble_stats(np.stack([u[m] for m in mem]), S.TWO_PI)
+        ref = T.ensemble_stats(np.stack([u[m] for m in mem]), S.TWO_PI, prm)
         _check(p.ensemble_stats(N), ref, rtol)
+    # the vorticity magnitude field of one member
+    w = p.vorticity_magnitude(0).cpu().numpy()
+    wref = T.vorticity_magnitude(u[0], S.TWO_PI)
+    assert np.max(np.abs(w - wref)) <= rtol * np.max(wref)
+    p.close()
+
+
+def test_perturbed_taylor_green_energy_budget(lib):
+    """The paper's perturbed Taylor-Green workload (section 6.1: unit torus,
+    s = 1.5, 8 x 3 uniform first-harmonic perturbations per sample) as an
+    ensemble: the energy writer's time series obeys dE/dt = -D with D the
+    dissipation writer (trapezoidal in time, error O(dt^3) per step), the
+    enstrophy writer matches the oracle, and the vorticity field is finite."""
+    from paper_2401_09843_gb300 import binding as B
+    N, M, dt, nsteps = 32, 4, 2e-4, 10
+    prm = S.Params(L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+    p = B.Plan([N] * M, B.NS3D_F64, L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+    # the perturbations are drawn per component; the flow starts from their
+    # divergence-free part (the solver evolves P u0)
+    u = [S.leray(I.perturbed_taylor_green(N, seed=601, member=m), 1.0) for m in range(M)]
+    for m, x in enumerate(u):
+        p.set_initial(m, x)
+    series = [p.ensemble_stats(N, fields=False)]
+    for _ in range(nsteps):
+        p.step(1)
+        series.append(p.ensemble_stats(N, fields=False))
+    for a, b in zip(series[:-1], series[1:]):
+        dE = b["energy"] - a["energy"]
+        assert abs(dE + 0.5 * dt * (a["dissipation"] + b["dissipation"])) < 1e-5 * abs(dE)
+    uT = [S.integrate(x, prm, nsteps)[0] for x in u]
+    ref = T.ensemble_stats(np.stack(uT), 1.0, prm)
+    last = series[-1]
+    assert abs(last["enstrophy"] - ref["enstrophy"]) < 1e-11 * ref["enstrophy"]
+    assert abs(last["dissipation"] - ref["dissipation"]) < 1e-11 * ref["dissipation"]
+    assert np.max(np.abs(np.asarray(last["enstrophy_spectrum"]) - ref["enstrophy_spectrum"])) \
+        < 1e-11 * np.max(ref["enstrophy_spectrum"])
+    w = p.vorticity_magnitude(0).cpu().numpy()
+    assert np.all(np.isfinite(w)) and np.max(np.abs(w - T.vorticity_magnitude(uT[0], 1.0))) \
+        < 1e-10 * np.max(w)
     p.close()
 
 

@@ -145,3 +145,43 @@ def test_beltrami_gradient_closed_form():
     assert np.linalg.norm((pg - r ** (2 * n) * u0).ravel()) < 1e-13 * np.linalg.norm(u0.ravel())
     g_out = A.grad_band_energy(u0, prm, n, dt, 4.0, 6.0)
     assert np.max(np.abs(S.leray(g_out, TWO_PI))) < 1e-15
+
+
+def test_enstrophy_spectrum_pins():
+    """Beltrami field at shell K (omega = K u): Z(K) = K^2 E(K), zero on other
+    shells; a random divergence-free field: Z(K) = 1/2 sum |kappa|^2 |u|^2 by
+    shell (|kappa x u|^2 = |kappa|^2 |u|^2 when kappa . u = 0)."""
+    N, K = 16, 3
+    u = I.beltrami_abc(N, K=K)
+    E, Z = T.energy_spectrum(u), T.enstrophy_spectrum(u, S.TWO_PI)
+    assert abs(Z[K] - K * K * E[K]) < 1e-13 * Z[K]
+    assert np.sum(np.abs(np.delete(Z, K))) < 1e-13 * Z[K]
+    v = I.random_spectrum(N, seed=3, k0=3.0)
+    kx, ky, kz = S.wavenumbers(N)
+    k2 = (kx * kx + ky * ky + kz * kz).astype(float)
+    e = 0.5 * np.sum(np.abs(v) ** 2, axis=0) * S.half_weights(N) * k2
+    ref = np.bincount(np.broadcast_to(T.shell_index(N), e.shape).ravel(), weights=e.ravel(),
+                      minlength=N)[:N]
+    assert np.allclose(T.enstrophy_spectrum(v, S.TWO_PI), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_dissipation_rate_is_minus_dE_dt():
+    """D = sum lambda_k |u_k|^2 equals -Re<u, R(u)> (the nonlinear term
+    conserves energy under exact dealiasing)."""
+    N = 16
+    prm = S.Params(nu=0.02, eps0=1.0)
+    u = I.random_spectrum(N, seed=8, k0=3.0)
+    D = T.dissipation_rate(u, prm)
+    assert abs(D + S.inner(u, S.rhs(u, prm))) < 1e-12 * D
+
+
+def test_vorticity_magnitude_taylor_green():
+    """u = (sin x cos y cos z, -cos x sin y cos z, 0): omega = (-cos x sin y sin z,
+    -sin x cos y sin z, 2 sin x sin y cos z) by hand."""
+    N = 16
+    x = np.arange(N) * 2 * np.pi / N
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    w2 = ((np.cos(X) * np.sin(Y) * np.sin(Z)) ** 2 + (np.sin(X) * np.cos(Y) * np.sin(Z)) ** 2
+          + (2 * np.sin(X) * np.sin(Y) * np.cos(Z)) ** 2)
+    got = T.vorticity_magnitude(I.taylor_green(N), S.TWO_PI)
+    assert np.max(np.abs(got - np.sqrt(w2))) < 1e-13
