@@ -398,6 +398,7 @@ struct SpecArgs {
   long long m6, m3;    // member strides of Bh and of U
   SpecT<T> sp;         // parameters in the arithmetic type
   Ns3dCtrl* ctrl;
+  const T* lam;        // lambda_k by integer |k|^2 (evaluated in FP64 once), or null
 };
 
 template <typename T> NS3D_HD T ctrl_dt(const Ns3dCtrl& c);
@@ -447,7 +448,7 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, int m, int kx, int j) {
     const cplx<T> bb[3] = {cmake(t0.y, -t0.x), cmake(t1.y, -t1.x), cmake(t2.y, -t2.x)};
     const T kap2 = kx_ * kx_ + ky_ * ky_ + kz_ * kz_;
     const cplx<T> kb = (T(1) / kap2) * (kx_ * bb[0] + ky_ * bb[1] + kz_ * bb[2]);
-    const T lam = lambda_k<T>(k2, sp);
+    const T lam = a.lam ? a.lam[k2] : lambda_k<T>(k2, sp);
     // the dissipation acts on the field R is evaluated at: u_n at stages 0
     // and 1, the stage state at stages 2 and 3
     const cplx<T>* ue = (a.stage >= 2) ? a.us + m * a.m3 + off : u0;

@@ -45,7 +45,7 @@ struct Level {
   bool fused = false;     // the step uses the fused x pass (FP32 register sizes)
   bool a_valid = false;   // W1 holds the x-inverse of U0 (set by the last step)
   XFusedMaps maps{};      // TMA descriptors of W2 (Dq), U0, US for the fused x pass
-  void* lamT = nullptr;   // lambda_k by |k|^2 (fused levels)
+  void* lamT = nullptr;   // lambda_k by |k|^2 in the arithmetic type
   unsigned extra_tx = 0;  // test hook: bytes the first staged tile never delivers
 };
 
@@ -196,6 +196,7 @@ StageBufs level_bufs(Level& L, int m0) {
   b.us = static_cast<unsigned char*>(L.US) + (size_t)m0 * L.g.nU * L.g.esz;
   b.ctrl = L.ctrl + m0;
   b.fused = false;
+  b.lam = L.lamT;
   return b;
 }
 
@@ -205,7 +206,6 @@ ns3d_status enqueue_stage(Level& L, int stage, int m0, int nm, const cplx<T>* in
   StageBufs b = level_bufs(L, m0);
   b.fused = L.fused && stage >= 1 && m0 == 0 && nm == L.B;
   b.maps = &L.maps;
-  b.lam = L.lamT;
   b.extra_tx = L.extra_tx;
   return enqueue_rhs<T>(b, stage, nm, in, out, want_umax, s, tm);
 }
@@ -303,6 +303,7 @@ ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in
   a.m3 = g.nU;
   a.sp = spec_t<T>(b.sp);
   a.ctrl = b.ctrl;
+  a.lam = static_cast<const T*>(b.lam);
   if (stage == 1) NS3D_CK(launch_step_dt(b.ctrl, nm, b.sp, s));
   NS3D_CK(launch_spectral<T>(a, s));
   NS3D_MARK(6);
@@ -589,11 +590,9 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
     if (st != NS3D_OK) break;
     if (L.fused && !xfused_make_maps(&L.maps, g, L.B, L.W2, L.U0, L.US)) L.fused = false;
-    if (L.fused) {
-      if ((st = dev_alloc(p, &L.lamT, lambda_entries(g) * sizeof(float))) != NS3D_OK) break;
-      st = upload_lambda<float>(L, p->stream);
-      if (st != NS3D_OK) break;
-    }
+    if ((st = dev_alloc(p, &L.lamT, lambda_entries(g) * p->esz / 2)) != NS3D_OK) break;
+    st = dtype == NS3D_F32 ? upload_lambda<float>(L, p->stream) : upload_lambda<double>(L, p->stream);
+    if (st != NS3D_OK) break;
     if (cudaMemsetAsync(L.U0, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
         cudaMemsetAsync(L.US, 0, (size_t)L.B * g.nU * p->esz, p->stream) != cudaSuccess ||
         launch_ctrl_reset(L.ctrl, L.B, p->stream) != cudaSuccess)
