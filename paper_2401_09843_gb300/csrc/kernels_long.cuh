@@ -37,7 +37,7 @@ cudaError_t colfast3_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s
 }
 
 template <typename T, int N1, int N2, int N3>
-__global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR, 3)
+__global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR, sizeof(T) == 8 ? 4 : 3)
     k_zfast3(ZArgs<T> a, long long ntiles) {
   using S = ZFast3Shape<N1, N2, N3>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];

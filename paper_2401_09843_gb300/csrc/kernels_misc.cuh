@@ -80,11 +80,19 @@ cudaError_t launch_zpass(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t 
 #undef NS3D_ZF_GO
   }
   if (zfast3_available<T>(g.P) && 3 * g.h == g.P) {
+    if (sizeof(T) == 4) {
 #define NS3D_ZF3_GO(A, B, C) \
-    if (g.P == (A) * (B) * (C)) \
-      return zfast3_launch<float, A, B, C>(*reinterpret_cast<const ZArgs<float>*>(&a), nm, s);
-    NS3D_FOR_ZFAST3(NS3D_ZF3_GO)
+      if (g.P == (A) * (B) * (C)) \
+        return zfast3_launch<float, A, B, C>(*reinterpret_cast<const ZArgs<float>*>(&a), nm, s);
+      NS3D_FOR_ZFAST3(NS3D_ZF3_GO)
 #undef NS3D_ZF3_GO
+    } else {
+#define NS3D_ZF3D_GO(A, B, C) \
+      if (g.P == (A) * (B) * (C)) \
+        return zfast3_launch<double, A, B, C>(*reinterpret_cast<const ZArgs<double>*>(&a), nm, s);
+      NS3D_FOR_ZFAST3_F64(NS3D_ZF3D_GO)
+#undef NS3D_ZF3D_GO
+    }
   }
   return launch_zfused<T>(a, ns3d::launch_z(g, nm), s);
 }

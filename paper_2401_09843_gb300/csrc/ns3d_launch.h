@@ -133,10 +133,13 @@ cudaError_t zfast_init();
 
 template <typename T>
 bool zfast3_available(int P) {
-  if (sizeof(T) != 4) return false;
 #define NS3D_ZF3_CASE(A, B, C) \
   if (P == (A) * (B) * (C)) return true;
-  NS3D_FOR_ZFAST3(NS3D_ZF3_CASE)
+  if (sizeof(T) == 4) {
+    NS3D_FOR_ZFAST3(NS3D_ZF3_CASE)
+  } else {
+    NS3D_FOR_ZFAST3_F64(NS3D_ZF3_CASE)
+  }
 #undef NS3D_ZF3_CASE
   return false;
 }
@@ -172,6 +175,15 @@ cudaError_t kernels_init() {
                       zfused_init<T>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
+  if (sizeof(T) == 8) {
+#define NS3D_LONG64_INIT(A, B, C)                           \
+    {                                                       \
+      cudaError_t r = long_init<double, A, B, C>();         \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_ZFAST3_F64(NS3D_LONG64_INIT)
+#undef NS3D_LONG64_INIT
+  }
   if (sizeof(T) == 4) {
 #define NS3D_ZF_INIT(A, B)                                  \
     {                                                       \

@@ -364,3 +364,14 @@ def test_autotune_cache_file(tmp_path):
     P2 = int(subprocess.run([sys.executable, "-c", code], env=env, check=True,
                             stdout=subprocess.PIPE, text=True).stdout.split()[-1])
     assert P2 == P1 and len(cache.read_text().splitlines()) == 1
+
+
+@pytest.mark.parametrize("N", [32, 256])
+def test_fp64_three_pass_z_pass(B, N):
+    """FP64 at P = 3N/2 (the three-pass register z pass where it exists):
+    sparse RHS against the Galerkin product, and CFL steps at N = 32."""
+    prm = S.Params(nu=0.0, eps0=1.0)
+    uh = I.sparse_random(N, seed=N + 9, nmodes=40)
+    p = plan(B, [N], B.NS3D_F64, nu=0.0, eps0=1.0, n_pad=3 * N // 2)
+    assert rel(p.eval_rhs(0, uh).cpu().numpy(), S.rhs_by_convolution(uh, prm)) < TOL64
+    p.close()
