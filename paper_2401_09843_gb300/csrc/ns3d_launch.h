@@ -57,6 +57,15 @@ cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaS
     NS3D_FOR_COLFAST3(NS3D_CF3_GO)
 #undef NS3D_CF3_GO
   }
+  if (sizeof(T) == 8 && 3 * a.h == a.pl.n && rows32 && (padded_inverse || truncated_forward)) {
+    const ColArgs<double>& ad = *reinterpret_cast<const ColArgs<double>*>(&a);
+#define NS3D_CF3D_GO(A, B, C)                                                        \
+    if (a.pl.n == (A) * (B) * (C))                                                   \
+      return kind == COL_INV_CC ? colfast3_launch<double, +1, A, B, C>(ad, L, s)    \
+                                : colfast3_launch<double, -1, A, B, C>(ad, L, s);
+    NS3D_FOR_ZFAST3_F64(NS3D_CF3D_GO)
+#undef NS3D_CF3D_GO
+  }
   if (sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
     const ColArgs<float>& af = *reinterpret_cast<const ColArgs<float>*>(&a);
 #define NS3D_CF_GO(A, B)                                                          \
