@@ -37,7 +37,8 @@ cudaError_t colfast3_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s
 }
 
 template <typename T, int N1, int N2, int N3>
-__global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR, sizeof(T) == 8 ? 4 : 3)
+__global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR,
+                                  sizeof(T) == 8 ? (ZFast3Shape<N1, N2, N3>::NTHR >= 128 ? 2 : 4) : 3)
     k_zfast3(ZArgs<T> a, long long ntiles) {
   using S = ZFast3Shape<N1, N2, N3>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
@@ -113,18 +114,23 @@ cudaError_t zfast3_launch(const ZArgs<T>& a, int nm, cudaStream_t s) {
 }
 
 template <typename T, int N1, int N2, int N3>
-cudaError_t long_init() {
+cudaError_t zfast3_init() {
   static_assert(zfast3_smem<T, N1, N2, N3>() <= 227 * 1024, "three-pass z: shared memory");
+  return cudaFuncSetAttribute((const void*)k_zfast3<T, N1, N2, N3>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+template <typename T, int N1, int N2, int N3>
+cudaError_t long_init() {
   static_assert(ColFast3Shape<N1, N2, N3>::SM_ELEMS * sizeof(cplx<T>) <= 227 * 1024,
                 "three-pass column: shared memory");
-  const void* f[3] = {(const void*)k_colfast3<T, +1, N1, N2, N3>,
-                      (const void*)k_colfast3<T, -1, N1, N2, N3>,
-                      (const void*)k_zfast3<T, N1, N2, N3>};
+  const void* f[2] = {(const void*)k_colfast3<T, +1, N1, N2, N3>,
+                      (const void*)k_colfast3<T, -1, N1, N2, N3>};
   for (const void* k : f) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return zfast3_init<T, N1, N2, N3>();
 }
 
 }  // namespace ns3d
@@ -137,4 +143,12 @@ cudaError_t long_init() {
                                                           cudaStream_t);                      \
   template cudaError_t zfast3_launch<T, N1, N2, N3>(const ZArgs<T>&, int, cudaStream_t);      \
   template cudaError_t long_init<T, N1, N2, N3>();                                           \
+  template cudaError_t zfast3_init<T, N1, N2, N3>();                                         \
+  }
+
+// the z pass alone (a shape whose column tile would not fit in shared memory)
+#define NS3D_ZFAST3_VARIANT(T, N1, N2, N3)                                                    \
+  namespace ns3d {                                                                           \
+  template cudaError_t zfast3_launch<T, N1, N2, N3>(const ZArgs<T>&, int, cudaStream_t);      \
+  template cudaError_t zfast3_init<T, N1, N2, N3>();                                         \
   }

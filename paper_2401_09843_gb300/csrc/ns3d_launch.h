@@ -39,6 +39,8 @@ template <typename T, int N1, int N2, int N3>
 cudaError_t zfast3_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
 template <typename T, int N1, int N2, int N3>
 cudaError_t long_init();
+template <typename T, int N1, int N2, int N3>
+cudaError_t zfast3_init();
 
 // A column pass: the register-resident kernel where one exists for (T, n, tile
 // width 16) or the three-pass one for long n, the generic tile kernel otherwise.
@@ -63,7 +65,7 @@ cudaError_t launch_col(const ColArgs<T>& a, ColKind kind, const Launch& L, cudaS
     if (a.pl.n == (A) * (B) * (C))                                                   \
       return kind == COL_INV_CC ? colfast3_launch<double, +1, A, B, C>(ad, L, s)    \
                                 : colfast3_launch<double, -1, A, B, C>(ad, L, s);
-    NS3D_FOR_ZFAST3_F64(NS3D_CF3D_GO)
+    NS3D_FOR_COLFAST3_F64(NS3D_CF3D_GO)
 #undef NS3D_CF3D_GO
   }
   if (sizeof(T) == 4 && a.W == 16 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
@@ -185,12 +187,19 @@ cudaError_t kernels_init() {
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   if (sizeof(T) == 8) {
+#define NS3D_Z64_INIT(A, B, C)                              \
+    {                                                       \
+      cudaError_t r = zfast3_init<double, A, B, C>();       \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_ZFAST3_F64(NS3D_Z64_INIT)
+#undef NS3D_Z64_INIT
 #define NS3D_LONG64_INIT(A, B, C)                           \
     {                                                       \
       cudaError_t r = long_init<double, A, B, C>();         \
       if (r != cudaSuccess) return r;                       \
     }
-    NS3D_FOR_ZFAST3_F64(NS3D_LONG64_INIT)
+    NS3D_FOR_COLFAST3_F64(NS3D_LONG64_INIT)
 #undef NS3D_LONG64_INIT
   }
   if (sizeof(T) == 4) {

@@ -41,6 +41,13 @@ def test_library_exports_every_header_function(built):
     assert sorted(binding.SYMBOLS) == names
 
 
+def test_library_resolves_every_symbol_at_load(built):
+    """Immediate binding: an undefined symbol (e.g. a kernel template that no
+    translation unit instantiates) fails here, not on the GPU machine."""
+    import os
+    ctypes.CDLL(built.LIB, mode=os.RTLD_NOW | os.RTLD_LOCAL)
+
+
 def test_status_strings_and_defaults(built):
     from paper_2401_09843_gb300 import binding
     lib = binding.load()

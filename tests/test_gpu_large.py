@@ -48,7 +48,8 @@ def test_rhs_largest_grids_sparse_field(B, N, dt):
     K, V = I.sparse_modes(N, seed=N + 5, nmodes=40)
     assert np.max(np.abs(K[:, :2])) > N // 2 - 64     # modes near the band edge
     Ko, Rref = S.rhs_sparse(K, V, N, prm)
-    p = B.Plan([N], dtype, nu=0.0, eps0=1.0)
+    # P = 3N/2 explicitly: the three-pass register z kernels of both precisions
+    p = B.Plan([N], dtype, nu=0.0, eps0=1.0, n_pad=3 * N // 2)
     p.test_poison_workspaces()          # every workspace read must have been written
     u, _ = on_device(torch, K, V, N, cdt)
     R = p.eval_rhs(0, u)
