@@ -407,13 +407,30 @@ def cpu_baseline():
                       f"initial-data family and parameters, single thread; {sec:.2f} s"}
 
 
+def oracle_step_seconds(N: int, warmup: int, steps: int):
+    """Per-step wall seconds of `steps` oracle RK3 steps at N^3 after `warmup`
+    untimed ones, all in one fresh single-threaded process."""
+    code = (
+        "import time, sys; sys.path.insert(0, %r)\n"
+        "import ns3d_inputs as I\n"
+        "from oracle import solver as S\n"
+        "u = I.random_spectrum(%d, seed=20240001)\n"
+        "prm = S.Params(eps0=1.0, cfl=0.5)\n"
+        "for _ in range(%d): u = S.rk3_step(u, prm)[0]\n"
+        "for _ in range(%d):\n"
+        "    t = time.perf_counter(); u = S.rk3_step(u, prm)[0]; print(time.perf_counter() - t)\n"
+        % (ROOT, N, warmup, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, text=True,
+                         check=True)
+    return [float(x) for x in out.stdout.split()]
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    N = 32
-    for _ in range(args.warmup):
-        oracle_sample_seconds(N, 1)
-    per = [oracle_sample_seconds(N, 1) for _ in range(args.steps)]
+    N = 16      # one oracle RK3 step at 16^3 per timed step: the whole run stays within minutes
+    per = oracle_step_seconds(N, args.warmup, args.steps)
     tot = sum(per)
     value = N ** 3 * args.steps / tot
     line = {
