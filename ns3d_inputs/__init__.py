@@ -203,6 +203,30 @@ def perturbed_taylor_green(N: int, seed: int, member: int = 0,
     return coefficients_of(u)
 
 
+def cylindrical_shear_flow(N: int, seed: int, member: int = 0, rho: float = 0.05,
+                           delta: float = 0.025, p: int = 10) -> np.ndarray:
+    """Cylindrical shear flow initial measure on the unit torus (L = 1), the
+    paper's section 6.2: u = tanh(2 pi (r - 0.25) / rho) (rho = 0: -1 for
+    r <= 0.25, else 1), v = w = 0, with
+    r^2 = (y - 0.5 + s_y(x))^2 + (z - 0.5 + s_z(x))^2 and
+    s_d(x) = delta sum_{k=1..p} a_k^d sin(2 pi k x - b_k^d), a ~ U[0, 1],
+    b ~ U[0, 2 pi] independent per sample and direction."""
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), int(member), 67])))
+    a = rng.uniform(0.0, 1.0, size=(2, p))
+    b = rng.uniform(0.0, 2 * np.pi, size=(2, p))
+    X, Y, Z = _grid(N, 1.0)
+    k = np.arange(1, p + 1)
+    sig = [delta * np.sum(a[d][:, None, None, None] *
+                          np.sin(2 * np.pi * k[:, None, None, None] * X[None] - b[d][:, None, None, None]),
+                          axis=0) for d in range(2)]
+    r = np.sqrt((Y - 0.5 + sig[0]) ** 2 + (Z - 0.5 + sig[1]) ** 2)
+    if rho > 0:
+        ux = np.tanh(2 * np.pi * (r - 0.25) / rho)
+    else:
+        ux = np.where(r <= 0.25, -1.0, 1.0)
+    return coefficients_of(np.stack([ux, np.zeros_like(ux), np.zeros_like(ux)]))
+
+
 def _energy_d1(uhat: np.ndarray) -> float:
     """1/2 sum over the full spectrum of |u_hat|^2 from D1 half storage."""
     w = np.full(uhat.shape[-1], 2.0)

@@ -185,3 +185,25 @@ def test_vorticity_magnitude_taylor_green():
           + (2 * np.sin(X) * np.sin(Y) * np.cos(Z)) ** 2)
     got = T.vorticity_magnitude(I.taylor_green(N), S.TWO_PI)
     assert np.max(np.abs(got - np.sqrt(w2))) < 1e-13
+
+
+def test_cylindrical_shear_flow_initial_data():
+    """rho = 0, delta = 0: u_x is -1 inside the unperturbed cylinder r <= 1/4
+    and 1 outside, so its mean is 1 - 2 (pi/16) up to the grid sampling of the
+    disc; the perturbed data are seeded per member and stay x-dependent."""
+    N = 64
+    u = I.cylindrical_shear_flow(N, seed=1, rho=0.0, delta=0.0)
+    # the k = 0 coefficient is the grid mean of the sampled step (the Nyquist
+    # modes the retained set drops do not touch it)
+    assert abs(u[0, 0, 0, 0].real - (1 - 2 * np.pi / 16)) < 0.02 and abs(u[0, 0, 0, 0].imag) < 1e-15
+    ux = S.to_physical(u, N)[0]
+    assert np.mean(np.abs(np.abs(ux) - 1.0) < 0.05) > 0.8     # away from the interface (Gibbs)
+    assert np.max(np.abs(u[1:])) < 1e-15
+    v0 = I.cylindrical_shear_flow(32, seed=1, member=0)
+    v1 = I.cylindrical_shear_flow(32, seed=1, member=1)
+    assert np.linalg.norm(v0 - v1) > 1e-3 * np.linalg.norm(v0)
+    assert np.array_equal(v0, I.cylindrical_shear_flow(32, seed=1, member=0))
+    # smooth profile: about +-1 (the truncation to the retained modes overshoots a little),
+    # with the x dependence of the displaced axis
+    w = S.to_physical(I.cylindrical_shear_flow(32, seed=2, rho=0.1), 32)[0]
+    assert np.max(np.abs(w)) < 1.2 and np.std(w.mean(axis=(1, 2))) > 1e-4
