@@ -224,6 +224,14 @@ ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);
  * NOT_SUPPORTED if N has a prime factor above 7. */
 ns3d_status ns3d_vorticity_magnitude(ns3d_plan plan, int member, void* out, int out_on_device);
 
+/* The velocity u(x) of member `member` at the N^3 grid points x_j = j L/N
+ * (inverse transform of the retained modes), as a real array [3][N][N][N]
+ * (z fastest) of the plan dtype in device or host memory per out_on_device:
+ * the samples whose one-point marginals the statistics compare across
+ * resolutions (section 6.1, mesh refinement).  Synchronises.  NOT_SUPPORTED if
+ * N has a prime factor above 7. */
+ns3d_status ns3d_physical_field(ns3d_plan plan, int member, void* out, int out_on_device);
+
 /* Diagnostic: advances every member by `nsteps` steps like ns3d_step, but
  * launches the kernels one by one (no graph) with CUDA events recorded on the
  * plan's stream around each of them, and adds the measured milliseconds of

@@ -23,6 +23,10 @@ formulas for them; the definitions used (both here and in the library) are:
                         -dE/dt of the spectral equation (section 2.3), whose
                         dealiased nonlinear term conserves energy
 * vorticity magnitude   |omega(x)| on the N^3 grid
+* 1-point Wasserstein distance between two ensembles (the paper's section 6.1
+  mesh-refinement measure): at each grid point the samples define empirical
+  one-point marginals mu_x, nu_x; W1(mu_x, nu_x) = integral |F_mu - F_nu| dt
+  (1D), and the distance is its mean over the points
 * Monte Carlo standard error of a sample mean: sqrt(var / M).
 
 Sample sets are merged with the pairwise formula of Chan, Golub and LeVeque
@@ -164,3 +168,27 @@ def welford(samples: np.ndarray):
         mean = mean + d / n
         m2 = m2 + d * (x - mean)
     return n, mean, m2
+
+
+def wasserstein1_1d(a: np.ndarray, b: np.ndarray) -> float:
+    """W1 between the empirical measures of the 1D samples a and b, from its
+    definition as the integral of |F_a(t) - F_b(t)| over t: both empirical
+    CDFs are constant between consecutive points of the merged samples."""
+    a = np.sort(np.asarray(a, dtype=np.float64).ravel())
+    b = np.sort(np.asarray(b, dtype=np.float64).ravel())
+    t = np.sort(np.concatenate([a, b]))
+    total = 0.0
+    for lo, hi in zip(t[:-1], t[1:]):
+        if hi > lo:
+            Fa = np.searchsorted(a, lo, side="right") / len(a)
+            Fb = np.searchsorted(b, lo, side="right") / len(b)
+            total += abs(Fa - Fb) * (hi - lo)
+    return total
+
+
+def wasserstein1_one_point(sa: np.ndarray, sb: np.ndarray) -> float:
+    """Mean over the points of W1 between the one-point marginals of two
+    ensembles of fields, sa (Ma, ...) and sb (Mb, ...) on the same points."""
+    sa = np.asarray(sa).reshape(sa.shape[0], -1)
+    sb = np.asarray(sb).reshape(sb.shape[0], -1)
+    return float(np.mean([wasserstein1_1d(sa[:, i], sb[:, i]) for i in range(sa.shape[1])]))

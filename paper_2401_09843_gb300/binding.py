@@ -27,7 +27,8 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_eval_rhs", "ns3d_adjoint_step", "ns3d_grad_band_energy",
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
            "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
-           "ns3d_set_clock", "ns3d_test_poison_workspaces", "ns3d_vorticity_magnitude"]
+           "ns3d_set_clock", "ns3d_test_poison_workspaces", "ns3d_vorticity_magnitude",
+           "ns3d_physical_field"]
 
 
 class Ns3dError(RuntimeError):
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         "ns3d_set_clock": (i, [vp, i, d, i]),
         "ns3d_test_poison_workspaces": (i, [vp]),
         "ns3d_vorticity_magnitude": (i, [vp, i, vp, i]),
+        "ns3d_physical_field": (i, [vp, i, vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,6 +294,15 @@ class Plan:
             res[k] = getattr(st, k)
         res["members"] = st.members
         return res
+
+    def physical_field(self, member: int):
+        """u(x) on the member's N^3 grid: a CUDA tensor [3][N][N][N]."""
+        n = self.N[member]
+        rdt = self.torch.float32 if self.dtype == NS3D_F32 else self.torch.float64
+        out = self.torch.empty((3, n, n, n), dtype=rdt, device="cuda")
+        _check(self.lib.ns3d_physical_field(self.h, member, ctypes.c_void_p(out.data_ptr()), 1),
+               "ns3d_physical_field")
+        return out
 
     def vorticity_magnitude(self, member: int):
         """|omega(x)| on the member's N^3 grid: a CUDA tensor [N][N][N]."""

@@ -268,8 +268,10 @@ __global__ void k_magnitude(const T* v, T* out, long long N3) {
   }
 }
 
+// what = 0: the velocity [3][N][N][N]; what = 1: |omega| [N][N][N]
 template <typename T>
-ns3d_status vorticity_impl(ns3d_plan p, const LevelView& L, int idx, void* out, int on_device) {
+ns3d_status physical_impl(ns3d_plan p, const LevelView& L, int idx, void* out, int on_device,
+                          int what) {
   const Geom& g = *L.g;
   const int N = g.N, h = g.h;
   const long long N3 = (long long)N * N * N;
@@ -289,15 +291,19 @@ ns3d_status vorticity_impl(ns3d_plan p, const LevelView& L, int idx, void* out, 
   cplx<T>* twN = static_cast<cplx<T>*>(alloc(sizeof(cplx<T>) * N));
   cplx<T>* W = static_cast<cplx<T>*>(alloc(sizeof(cplx<T>) * nc));
   cplx<T>* A = static_cast<cplx<T>*>(alloc(sizeof(cplx<T>) * nc));
-  T* phys = static_cast<T*>(alloc(sizeof(T) * 3 * N3));
-  T* mag = on_device ? static_cast<T*>(out) : static_cast<T*>(alloc(sizeof(T) * N3));
+  // phys: the three components on the grid; mag: the result ([3][N^3] velocity
+  // written in place, or [N^3] |omega|); the caller's device buffer when it has one
+  const long long nout = what == 0 ? 3 * N3 : N3;
+  T* mag = on_device ? static_cast<T*>(out) : static_cast<T*>(alloc(sizeof(T) * nout));
+  T* phys = what == 0 ? mag : static_cast<T*>(alloc(sizeof(T) * 3 * N3));
   bool ok = twN && W && A && phys && mag;
   if (ok) {
     std::vector<cplx<T>> tw = make_twiddles<T>(N);
     const cplx<T>* u = static_cast<const cplx<T>*>(L.U0) + idx * g.nU;
     ok = cudaMemcpyAsync(twN, tw.data(), sizeof(cplx<T>) * N, cudaMemcpyHostToDevice, s) == cudaSuccess &&
          cudaStreamSynchronize(s) == cudaSuccess;
-    k_curl<T><<<grid_of((long long)N * N * h), 256, 0, s>>>(u, W, N, T(L.sp.kscale));
+    if (what == 1) k_curl<T><<<grid_of((long long)N * N * h), 256, 0, s>>>(u, W, N, T(L.sp.kscale));
+    else ok = ok && cudaMemcpyAsync(W, u, sizeof(cplx<T>) * nc, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     // inverse x and y without padding, then c2r along z: as for the statistics
     ColArgs<T> ax = args_inv_x<T>(g, W, A, twN);
     ax.pl = g.plN; ax.nrow_out = N; ax.W = g.WcN; ax.ldw = g.ldwcN;
@@ -316,11 +322,11 @@ ns3d_status vorticity_impl(ns3d_plan p, const LevelView& L, int idx, void* out, 
       const size_t smz = (size_t)4 * N * az.ldw * sizeof(cplx<T>);
       cudaFuncSetAttribute((const void*)k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
       k_zinv<T><<<dim3(cdiv(N, az.W), N), 128, smz, s>>>(az);
-      k_magnitude<T><<<grid_of(N3), 256, 0, s>>>(phys, mag, N3);
+      if (what == 1) k_magnitude<T><<<grid_of(N3), 256, 0, s>>>(phys, mag, N3);
       ok = cudaGetLastError() == cudaSuccess;
     }
     if (ok && !on_device)
-      ok = cudaMemcpyAsync(out, mag, sizeof(T) * N3, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+      ok = cudaMemcpyAsync(out, mag, sizeof(T) * nout, cudaMemcpyDeviceToHost, s) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   }
   for (void* q : tmp) cudaFree(q);
@@ -328,16 +334,24 @@ ns3d_status vorticity_impl(ns3d_plan p, const LevelView& L, int idx, void* out, 
   return ok ? NS3D_OK : NS3D_ERR_CUDA;
 }
 
-}  // namespace
-
-extern "C" ns3d_status ns3d_vorticity_magnitude(ns3d_plan p, int member, void* out, int on_device) {
+ns3d_status physical_entry(ns3d_plan p, int member, void* out, int on_device, int what) {
   if (!p || !out) return NS3D_ERR_INVALID_ARG;
   LevelView L;
   int idx = 0;
   if (!member_view(p, member, &L, &idx)) return NS3D_ERR_INVALID_ARG;
   PlanDeviceGuard dg(p);
-  return plan_dtype(p) == NS3D_F32 ? vorticity_impl<float>(p, L, idx, out, on_device)
-                                   : vorticity_impl<double>(p, L, idx, out, on_device);
+  return plan_dtype(p) == NS3D_F32 ? physical_impl<float>(p, L, idx, out, on_device, what)
+                                   : physical_impl<double>(p, L, idx, out, on_device, what);
+}
+
+}  // namespace
+
+extern "C" ns3d_status ns3d_vorticity_magnitude(ns3d_plan p, int member, void* out, int on_device) {
+  return physical_entry(p, member, out, on_device, 1);
+}
+
+extern "C" ns3d_status ns3d_physical_field(ns3d_plan p, int member, void* out, int on_device) {
+  return physical_entry(p, member, out, on_device, 0);
 }
 
 extern "C" ns3d_status ns3d_ensemble_stats(ns3d_plan p, int level_N, ns3d_stats* out) {

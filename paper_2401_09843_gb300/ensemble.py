@@ -71,3 +71,20 @@ def allreduce_stats(stats: dict, group=None) -> dict:
     for p in parts[1:]:
         acc = merge_stats(acc, p)
     return acc
+
+
+def wasserstein1_one_point(sa, sb) -> float:
+    """1-point Wasserstein distance between two ensembles of fields on the same
+    points (mesh-refinement studies, section 6.1): the mean over the points of
+    W1 between the empirical one-point marginals.  sa (Ma, ...), sb (Mb, ...).
+    Equal sample counts use the sorted-sample form mean |a_(i) - b_(i)|; other
+    counts integrate |F_a - F_b| between the merged sorted samples."""
+    a = np.sort(np.asarray(sa, dtype=np.float64).reshape(np.shape(sa)[0], -1), axis=0)
+    b = np.sort(np.asarray(sb, dtype=np.float64).reshape(np.shape(sb)[0], -1), axis=0)
+    if a.shape[0] == b.shape[0]:
+        return float(np.mean(np.abs(a - b)))
+    t = np.sort(np.concatenate([a, b], axis=0), axis=0)              # (Ma + Mb, points)
+    lo, dt = t[:-1], np.diff(t, axis=0)
+    Fa = np.stack([np.sum(a <= x[None, :], axis=0) for x in lo]) / a.shape[0]
+    Fb = np.stack([np.sum(b <= x[None, :], axis=0) for x in lo]) / b.shape[0]
+    return float(np.mean(np.sum(np.abs(Fa - Fb) * dt, axis=0)))

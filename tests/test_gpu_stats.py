@@ -152,3 +152,36 @@ def test_cylindrical_shear_flow_mean_and_variance(lib):
         assert abs(p.get_state(m).cpu().numpy()[0, 0, 0, 0] - u[m][0, 0, 0, 0]) < 1e-15
     assert np.max(np.asarray(g["var"])[0]) > 0      # the samples differ
     p.close()
+
+
+def test_physical_field_and_mesh_refinement_measures(lib):
+    """Mesh refinement of the perturbed Taylor-Green ensemble (section 6.1) at
+    small scale: the same 6 samples at 16^3 and 32^3 (FP64), fields from
+    ns3d_physical_field (checked against the oracle), compared on the coarse
+    grid points: sample, mean and variance differences and the 1-point
+    Wasserstein distance of the u_x marginals (package = oracle definition;
+    W1 >= the mean difference pointwise)."""
+    from paper_2401_09843_gb300 import binding as B
+    from paper_2401_09843_gb300.ensemble import wasserstein1_one_point
+    M, dt, n = 6, 2e-4, 5
+    prm = S.Params(L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+    fields = {}
+    for N in (16, 32):
+        u = [S.leray(I.perturbed_taylor_green(N, seed=601, member=m), 1.0) for m in range(M)]
+        p = B.Plan([N] * M, B.NS3D_F64, L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+        for m, x in enumerate(u):
+            p.set_initial(m, x)
+        p.step(n)
+        f = np.stack([p.physical_field(m).cpu().numpy() for m in range(M)])
+        ref = T.physical_on_grid(S.integrate(u[0], prm, n)[0])
+        assert np.max(np.abs(f[0] - ref)) < 1e-11 * np.max(np.abs(ref))
+        fields[N] = f[:, 0]
+        p.close()
+    coarse, fine = fields[16], fields[32][:, ::2, ::2, ::2]
+    w = wasserstein1_one_point(coarse, fine)
+    assert abs(w - T.wasserstein1_one_point(coarse, fine)) < 1e-12
+    mean_err = np.mean(np.abs(coarse.mean(axis=0) - fine.mean(axis=0)))
+    var_err = np.mean(np.abs(coarse.var(axis=0, ddof=1) - fine.var(axis=0, ddof=1)))
+    sample_err = np.mean(np.abs(coarse - fine))
+    assert mean_err - 1e-15 <= w <= sample_err + 1e-15
+    assert 0 < w < 0.1 and var_err >= 0

@@ -207,3 +207,26 @@ def test_cylindrical_shear_flow_initial_data():
     # with the x dependence of the displaced axis
     w = S.to_physical(I.cylindrical_shear_flow(32, seed=2, rho=0.1), 32)[0]
     assert np.max(np.abs(w)) < 1.2 and np.std(w.mean(axis=(1, 2))) > 1e-4
+
+
+def test_wasserstein_pins():
+    """W1 closed forms: Dirac masses |a - b|; a shift by c gives |c|;
+    (delta_0 + delta_1)/2 against delta_1/2 gives 1/2; W1 >= |mean difference|;
+    equal counts: the mean distance of the sorted samples."""
+    rng = np.random.default_rng(4)
+    assert abs(T.wasserstein1_1d([0.3], [1.7]) - 1.4) < 1e-15
+    x = rng.standard_normal(50)
+    assert abs(T.wasserstein1_1d(x, x + 0.25) - 0.25) < 1e-12
+    assert abs(T.wasserstein1_1d([0.0, 1.0], [0.5]) - 0.5) < 1e-15
+    a, b = rng.standard_normal(40), 0.5 + 2 * rng.standard_normal(25)
+    assert T.wasserstein1_1d(a, b) >= abs(a.mean() - b.mean()) - 1e-12
+    c = rng.standard_normal(40)
+    assert abs(T.wasserstein1_1d(a, c) - np.mean(np.abs(np.sort(a) - np.sort(c)))) < 1e-12
+
+
+def test_package_wasserstein_matches_oracle():
+    from paper_2401_09843_gb300.ensemble import wasserstein1_one_point
+    rng = np.random.default_rng(5)
+    a, b, c = rng.standard_normal((8, 3, 4)), rng.standard_normal((8, 3, 4)), rng.standard_normal((5, 3, 4))
+    assert abs(wasserstein1_one_point(a, b) - T.wasserstein1_one_point(a, b)) < 1e-12
+    assert abs(wasserstein1_one_point(a, c) - T.wasserstein1_one_point(a, c)) < 1e-12
