@@ -77,6 +77,25 @@ def bench_ensemble(B, torch, steps: int, warmup: int, to_t: float = 0.0):
             "ms_per_step": ms / steps, "value": pts * steps / (ms * 1e-3), "unit": UNIT,
             "samples_steps_per_s": len(Ns) * steps / (ms * 1e-3),
             "gpu_launches_per_step": plan.info(0)["launches_per_step"]}
+    if to_t > 0:
+        # the workload's horizon: every member to t = to_t (a member stops at it
+        # while the others go on), then the FP64 statistics of each level
+        t0 = time.perf_counter()
+        done = steps + warmup
+        while done < 20000:
+            plan.step(50, t_end=to_t)
+            done += 50
+            plan.synchronize()
+            if min(plan.clock(m)[0] for m in range(len(Ns))) >= to_t * (1 - 1e-12):
+                break
+        wall = time.perf_counter() - t0
+        levels = {}
+        for N, M, _ in ENSEMBLE_LEVELS:
+            st = plan.ensemble_stats(N, fields=False)
+            levels[str(N)] = {k: st[k] for k in ("members", "energy", "energy_se", "enstrophy",
+                                                 "enstrophy_se", "dissipation", "dissipation_se")}
+            levels[str(N)]["steps_to_t"] = max(plan.clock(m)[1] for m in range(len(Ns)) if Ns[m] == N)
+        info["to_t"] = {"t": to_t, "graph_steps": done, "wall_s_after_timed": wall, "levels": levels}
     plan.close()
     return info
 
@@ -599,7 +618,7 @@ def main():
         "status_ok": status_ok,
     }
     if not args.no_extras and world == 1:
-        line["batched_ensemble"] = bench_ensemble(B, torch, steps=10, warmup=2)
+        line["batched_ensemble"] = bench_ensemble(B, torch, steps=10, warmup=2, to_t=1.0)
         line["plain_fp64"] = bench_plain_fp64(B, torch, N, steps=3)
         line["largest"] = bench_largest(B, torch)
         line["cufft_pipeline"] = bench_cufft(torch, N)
