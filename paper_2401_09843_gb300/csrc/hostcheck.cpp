@@ -1,5 +1,5 @@
 // CPU emulation of the solver's kernels, block by block with one thread per
-// block, for the index-logic tests (tests/test_hostcheck.py).  It runs the
+// block, for the index-logic tests (tests/test_abi_host.py).  It runs the
 // exact block bodies of ns3d_blocks.cuh with the launch shapes and strides of
 // ns3d_geom.h, so a wrong stride, tile bound, padding map or pairing shows up
 // against the oracle on the CPU before any GPU run.  Not part of the solver's
