@@ -101,9 +101,25 @@ def bench_ensemble(B, torch, steps: int, warmup: int, to_t: float = 0.0):
 
 
 def bench_plain_fp64(B, torch, N: int, steps: int):
+    """The plain FP64 path on the main workload, and the FP32 path's relative
+    L2 error against it: one right-hand side, and the state after 10 steps."""
     import ns3d_inputs as I
+    u0 = I.random_spectrum(N, seed=20240001)
+    res = {}
+    for name, dtype in (("f32", B.NS3D_F32), ("f64", B.NS3D_F64)):
+        p = B.Plan([N], dtype, eps0=1.0, cfl=0.5)
+        r = p.eval_rhs(0, u0).to(torch.complex128)
+        p.set_initial(0, u0)
+        p.step(10)
+        res[name] = (r, p.get_state(0).to(torch.complex128))
+        p.close()
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    err = {"rhs_rel_l2": rel(res["f32"][0], res["f64"][0]),
+           "state_after_10_steps_rel_l2": rel(res["f32"][1], res["f64"][1])}
+    del res
+    torch.cuda.empty_cache()
     plan = B.Plan([N], B.NS3D_F64, eps0=1.0, cfl=0.5)
-    plan.set_initial(0, I.random_spectrum(N, seed=20240001))
+    plan.set_initial(0, u0)
     plan.step(1)
     plan.synchronize()
     stream = torch.cuda.current_stream()
@@ -115,7 +131,7 @@ def bench_plain_fp64(B, torch, N: int, steps: int):
     ms = e0.elapsed_time(e1)
     plan.close()
     return {"N": N, "steps": steps, "ms_per_step": ms / steps,
-            "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT}
+            "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT, "f32_error_vs_f64": err}
 
 
 def embedded_ic(torch, N: int, cdtype, seed: int, k0: float, n0: int = 256):
@@ -254,16 +270,17 @@ def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
     `every` steps, fixed dt) at 128^3: wall time of one gradient, forward
     recomputation included, against `nsteps` forward steps."""
     import ns3d_inputs as I
-    out = {}
+    out, grads = {}, {}
     for dt_name, dtype in (("f32", B.NS3D_F32), ("f64", B.NS3D_F64)):
         plan = B.Plan([N], dtype, eps0=1.0, dt_fixed=0.005)
         plan.set_initial(0, I.random_spectrum(N, seed=20240004))
         plan.grad_band_energy(0, 8.0, 16.0, 2, checkpoint_every=2)     # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=every)
+        g = plan.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=every)
         torch.cuda.synchronize()
         tg = time.perf_counter() - t0
+        grads[dt_name] = g.to(torch.complex128)
         plan.step(2)
         plan.synchronize()
         t0 = time.perf_counter()
@@ -272,6 +289,9 @@ def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
         tf = time.perf_counter() - t0
         plan.close()
         out[dt_name] = {"gradient_s": tg, "forward_s": tf, "ratio": tg / tf}
+    d = grads["f32"] - grads["f64"]
+    out["f32_gradient_rel_l2_vs_f64"] = float(torch.linalg.vector_norm(d) /
+                                              torch.linalg.vector_norm(grads["f64"]))
     return {"N": N, "steps": nsteps, "checkpoint_every": every, **out}
 
 
