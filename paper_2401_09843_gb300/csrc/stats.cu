@@ -1,8 +1,10 @@
 // Ensemble statistics of one level (writers of section 2.4; the empirical
 // measure of Algorithm 1 step 3), accumulated in FP64 on the device.
 //
-// Per member: the energy spectrum and the three axis spectra are histogrammed
-// from the stored coefficients (FP64 block histograms, atomics across blocks);
+// Per member: the energy and enstrophy spectra, the three axis spectra and the
+// dissipation rate are histogrammed from the stored coefficients in FP64 with
+// compensated (TwoSum/Neumaier) sums merged in a fixed order, so that the
+// result is reproducible bit for bit and its error stays a few ulps;
 // the second-order structure function follows from the axis spectra,
 //   S2(r_j) = (1/3) sum_d sum_k e_d(k) 2 (1 - cos(2 pi k j / N)).
 // For the pointwise fields the member's velocity is taken to the N^3 grid
@@ -23,40 +25,149 @@ namespace {
 // e_z; [4N, 5N) Z(K); [5N] D = sum lambda_k |u_hat_k|^2 (full spectrum)
 NS3D_HDC int hist_len(int N) { return 5 * N + 1; }
 
+// A compensated pair: the value s + c, c holding the rounding errors of the
+// additions that made s.
+struct CSum {
+  double s, c;
+};
+
+// Knuth's TwoSum: s = fl(a.s + b.s) and its exact error e = (a.s + b.s) - s,
+// folded into the compensation (Neumaier's compensated summation, written for
+// pairs so that partial sums merge in any tree).  Commutative, so every lane of
+// a butterfly ends with the same pair.
+NS3D_HD CSum csum_merge(CSum a, CSum b) {
+  const double s = a.s + b.s;
+  const double bp = s - a.s;
+  const double e = (a.s - (s - bp)) + (b.s - bp);
+  return {s, (a.c + b.c) + e};
+}
+
+__device__ CSum csum_shfl_down(CSum a, int d) {
+  return {__shfl_down_sync(0xffffffffu, a.s, d), __shfl_down_sync(0xffffffffu, a.c, d)};
+}
+
+// lane 0 receives the merge of the warp's 32 pairs (a fixed tree)
+__device__ CSum csum_warp(CSum a) {
+  for (int d = 16; d > 0; d >>= 1) a = csum_merge(a, csum_shfl_down(a, d));
+  return a;
+}
+
+// one bin of a histogram of pairs: sums in hs, compensations in hc
+__device__ void csum_bin_add(double* hs, double* hc, int i, CSum v) {
+  const CSum r = csum_merge(CSum{hs[i], hc[i]}, v);
+  hs[i] = r.s;
+  hc[i] = r.c;
+}
+
+// Spectra of one member, one block per kx plane, with compensated sums in a
+// fixed order (the result does not depend on scheduling).  Each warp owns a
+// histogram of pairs in shared memory and walks rows ky = warp, warp + nw, ...
+// 32 kz at a time.  Along a row |k| never decreases with kz, so the lanes
+// with one shell K form one run: a segmented suffix merge leaves the run's
+// total in its first lane, which alone adds it to the warp's bin K.  The e_z
+// bins take one lane each; e_y[ky], e_x[kx] and D are warp merges of lane
+// partials.  The warps' histograms are merged in warp order into one pair per
+// bin for this plane: part[kx][bin].
 template <typename T>
-__global__ void k_spectra(const cplx<T>* u, int N, double kscale2, SpecT<double> sp, double* hist) {
-  extern __shared__ double sh[];
+__global__ void k_spectra(const cplx<T>* u, int N, double kscale2, SpecT<double> sp, double2* part) {
+  extern __shared__ double sh[];   // [warp][sums HL | compensations HL]
   const int h = N / 2;
   const int L = hist_len(N);
-  for (int i = threadIdx.x; i < L; i += blockDim.x) sh[i] = 0.0;
+  const int nw = blockDim.x / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int i = threadIdx.x; i < 2 * L * nw; i += blockDim.x) sh[i] = 0.0;
   __syncthreads();
+  double* hs = sh + (size_t)warp * 2 * L;
+  double* hc = hs + L;
   const int kx = blockIdx.x;
-  for (int j = threadIdx.x; j < N * h; j += blockDim.x) {
-    const int ky = j / h, kz = j % h;
-    const long long plane = (long long)N * N * h;
-    const long long off = ((long long)kx * N + ky) * h + kz;
-    double e = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      const cplx<T> v = u[c * plane + off];
-      e += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-    }
-    if (kz > 0) e *= 2.0;     // the mirror mode -k
-    if (e == 0.0) continue;
-    const int sx = kx < h ? kx : kx - N;
+  const int sx = kx < h ? kx : kx - N;
+  const long long plane = (long long)N * N * h;
+  CSum ex{0.0, 0.0}, dd{0.0, 0.0};   // e_x[kx] (lane 0) and D (per lane)
+  for (int ky = warp; ky < N; ky += nw) {
     const int sy = ky < h ? ky : ky - N;
-    const int k2 = sx * sx + sy * sy + kz * kz;
-    const int K = shell_of(k2);
-    atomicAdd(&sh[K], 0.5 * e);
-    atomicAdd(&sh[2 * N + ky], e);
-    atomicAdd(&sh[3 * N + kz], e);
-    atomicAdd(&sh[N + kx], e);
-    atomicAdd(&sh[4 * N + K], 0.5 * kscale2 * (double)k2 * e);
-    atomicAdd(&sh[5 * N], lambda_k<double>(k2, sp) * e);
+    CSum ey{0.0, 0.0};
+    for (int k0 = 0; k0 < h; k0 += 32) {
+      const int kz = k0 + lane;
+      double e = 0.0, z = 0.0;
+      int K = -1;                      // lanes past the row: a run of their own, not stored
+      if (kz < h) {
+        const long long off = ((long long)kx * N + ky) * h + kz;
+        for (int c = 0; c < 3; ++c) {
+          const cplx<T> v = u[c * plane + off];
+          e += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        }
+        if (kz > 0) e *= 2.0;          // the mirror mode -k
+        const int k2 = sx * sx + sy * sy + kz * kz;
+        K = shell_of(k2);
+        z = 0.5 * kscale2 * (double)k2 * e;
+        ey = csum_merge(ey, CSum{e, 0.0});
+        dd = csum_merge(dd, CSum{lambda_k<double>(k2, sp) * e, 0.0});
+        csum_bin_add(hs, hc, 3 * N + kz, CSum{e, 0.0});
+      }
+      CSum E{0.5 * e, 0.0}, Z{z, 0.0};
+      for (int d = 1; d < 32; d <<= 1) {
+        const int Ko = __shfl_down_sync(0xffffffffu, K, d);
+        const CSum Eo = csum_shfl_down(E, d), Zo = csum_shfl_down(Z, d);
+        if (lane + d < 32 && Ko == K) {
+          E = csum_merge(E, Eo);
+          Z = csum_merge(Z, Zo);
+        }
+      }
+      const int Kp = __shfl_up_sync(0xffffffffu, K, 1);
+      if (K >= 0 && (lane == 0 || Kp != K)) {
+        csum_bin_add(hs, hc, K, E);
+        csum_bin_add(hs, hc, 4 * N + K, Z);
+      }
+      __syncwarp();
+    }
+    ey = csum_warp(ey);
+    if (lane == 0) {
+      csum_bin_add(hs, hc, 2 * N + ky, ey);
+      ex = csum_merge(ex, ey);
+    }
+  }
+  dd = csum_warp(dd);
+  if (lane == 0) {
+    csum_bin_add(hs, hc, N + kx, ex);
+    csum_bin_add(hs, hc, 5 * N, dd);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < L; i += blockDim.x)
-    if (sh[i] != 0.0) atomicAdd(&hist[i], sh[i]);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    CSum a{0.0, 0.0};
+    for (int w = 0; w < nw; ++w) a = csum_merge(a, CSum{sh[(size_t)w * 2 * L + i], sh[(size_t)w * 2 * L + L + i]});
+    part[(size_t)kx * L + i] = make_double2(a.s, a.c);
+  }
 }
+
+// hist[bin] = the planes' pairs merged in kx order, rounded once
+__global__ void k_spectra_merge(const double2* part, int N, int L, double* hist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+    CSum a{0.0, 0.0};
+    for (int kx = 0; kx < N; ++kx) {
+      const double2 q = part[(size_t)kx * L + i];
+      a = csum_merge(a, CSum{q.x, q.y});
+    }
+    hist[i] = a.s + a.c;
+  }
+}
+
+// warps per k_spectra block: as many histograms of pairs as fit, up to 8
+int spectra_warps(int N) {
+  const size_t per = 2 * sizeof(double) * (size_t)hist_len(N);
+  const size_t nw = (200 * 1024) / per;
+  return nw >= 8 ? 8 : (int)nw;
+}
+
+// host-side Neumaier sum
+struct HostCSum {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    const double t = s + x;
+    if (std::fabs(s) >= std::fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
 
 template <typename T>
 __global__ void k_zinv(ZInvArgs<T> a) {
@@ -114,7 +225,10 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
     for (void* q : tmp) cudaFree(q);
   };
   const int HL = hist_len(N);
+  const int nws = spectra_warps(N);
+  if (nws < 1) return NS3D_ERR_NOT_SUPPORTED;
   double* hist = static_cast<double*>(alloc(sizeof(double) * HL * M));
+  double2* part = static_cast<double2*>(alloc(sizeof(double2) * HL * (size_t)N));
   cplx<T>* twN = nullptr;
   double *mean = nullptr, *C = nullptr, *var = nullptr;
   T* phys = nullptr;
@@ -133,7 +247,7 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
       return NS3D_ERR_OUT_OF_MEMORY;
     }
   }
-  if (!hist) {
+  if (!hist || !part) {
     cleanup();
     return NS3D_ERR_OUT_OF_MEMORY;
   }
@@ -148,8 +262,10 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
   const cplx<T>* U0 = static_cast<const cplx<T>*>(L.U0);
   for (int m = 0; m < M && ok; ++m) {
     const cplx<T>* u = U0 + m * g.nU;
-    k_spectra<T><<<N, 256, sizeof(double) * HL, s>>>(u, N, L.sp.kscale * L.sp.kscale,
-                                                      spec_t<double>(L.sp), hist + (size_t)m * HL);
+    const size_t sms = 2 * sizeof(double) * (size_t)HL * nws;
+    cudaFuncSetAttribute((const void*)k_spectra<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    k_spectra<T><<<N, 32 * nws, sms, s>>>(u, N, L.sp.kscale * L.sp.kscale, spec_t<double>(L.sp), part);
+    k_spectra_merge<<<cdiv(HL, 256), 256, 0, s>>>(part, N, HL, hist + (size_t)m * HL);
     ok = cudaGetLastError() == cudaSuccess;
     if (!fields || !ok) continue;
     // inverse x and y without padding (n = N): column passes of the generic engine
@@ -192,26 +308,26 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
       zn(M), dn(M);
   for (int m = 0; m < M; ++m) {
     const double* H = &hh[(size_t)m * HL];
-    double e = 0.0, z = 0.0;
+    HostCSum e, z;
     for (int K = 0; K < N; ++K) {
       spec[(size_t)m * N + K] = H[K];
-      e += H[K];
+      e.add(H[K]);
       zspec[(size_t)m * N + K] = H[4 * N + K];
-      z += H[4 * N + K];
+      z.add(H[4 * N + K]);
     }
-    en[m] = e;
-    zn[m] = z;
+    en[m] = e.value();
+    zn[m] = z.value();
     dn[m] = H[5 * N];
     for (int j = 1; j <= N / 2; ++j) {
-      double acc = 0.0;
+      HostCSum acc;
       for (int d = 0; d < 3; ++d)
         for (int i = 0; i < N; ++i) {
           const double v = H[(d + 1) * N + i];
           if (v == 0.0) continue;
           const int k = (d < 2 && i >= N / 2) ? i - N : i;
-          acc += v * 2.0 * (1.0 - std::cos(2.0 * PI * (double)k * j / N));
+          acc.add(v * 2.0 * (1.0 - std::cos(2.0 * PI * (double)k * j / N)));
         }
-      s2[(size_t)m * (N / 2) + j - 1] = acc / 3.0;
+      s2[(size_t)m * (N / 2) + j - 1] = acc.value() / 3.0;
     }
   }
   auto mean_se = [&](const std::vector<double>& x, int n, double* mu, double* se) {

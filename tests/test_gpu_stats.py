@@ -185,3 +185,43 @@ def test_physical_field_and_mesh_refinement_measures(lib):
     sample_err = np.mean(np.abs(coarse - fine))
     assert mean_err - 1e-15 <= w <= sample_err + 1e-15
     assert 0 < w < 0.1 and var_err >= 0
+
+
+def _shell(k2):
+    K = np.floor(np.sqrt(k2.astype(np.float64))).astype(np.int64)
+    K += ((2 * K + 1) ** 2 <= 4 * k2)
+    K -= (K > 0) & ((2 * K - 1) ** 2 > 4 * k2)
+    return K
+
+
+@pytest.mark.parametrize("N", [48, 128])
+def test_spectra_are_compensated_and_reproducible(lib, N):
+    """Each spectrum bin is the exactly rounded sum of its modes within a few
+    ulps (compensated sums; a plain sum of ~10^5 terms drifts further), and two
+    calls agree bit for bit (a fixed merge order, no atomics)."""
+    import math
+    from paper_2401_09843_gb300 import binding as B
+    p = B.Plan([N], B.NS3D_F64, eps0=1.0)
+    p.set_initial(0, I.random_spectrum(N, seed=77, k0=0.3 * N))
+    a, b = p.ensemble_stats(N), p.ensemble_stats(N)
+    for k in ("spectrum", "enstrophy_spectrum", "s2"):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+    for k in ("energy", "enstrophy", "dissipation"):
+        assert a[k] == b[k], k
+    u = p.get_state(0).cpu().numpy()[..., : N // 2]       # drop the zero Nyquist kz plane
+    p.close()
+    e = np.sum(u.real ** 2 + u.imag ** 2, axis=0)
+    e[..., 1:] *= 2.0                                     # mirror modes -k
+    k = np.fft.fftfreq(N, 1.0 / N).astype(np.int64)
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + np.arange(N // 2)[None, None, :] ** 2
+    K = _shell(k2).ravel()
+    order = np.argsort(K, kind="stable")
+    bounds = np.searchsorted(K[order], np.arange(N + 1))
+    ev, zv = (0.5 * e).ravel()[order], (0.5 * k2 * e).ravel()[order]
+    spec = np.array([math.fsum(ev[bounds[i]:bounds[i + 1]]) for i in range(N)])
+    zspec = np.array([math.fsum(zv[bounds[i]:bounds[i + 1]]) for i in range(N)])
+    tol = 8 * np.finfo(np.float64).eps                    # per-mode rounding + the merge
+    assert np.all(np.abs(np.asarray(a["spectrum"]) - spec) <= tol * spec)
+    assert np.all(np.abs(np.asarray(a["enstrophy_spectrum"]) - zspec) <= tol * zspec)
+    assert abs(a["energy"] - math.fsum(ev)) <= tol * math.fsum(ev)
+    assert abs(a["enstrophy"] - math.fsum(zv)) <= tol * math.fsum(zv)
