@@ -134,6 +134,38 @@ def bench_plain_fp64(B, torch, N: int, steps: int):
             "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT, "f32_error_vs_f64": err}
 
 
+def bench_forms(B, torch, N: int, steps: int = 5):
+    """The advective (nonlinear_form = 1) and rotational (2) forms of the
+    nonlinear term at N^3 FP32 (generic tile kernels; 12 and 6 inverse
+    transforms instead of 3), and their relative L2 distance from the
+    divergence form's state after the timed steps."""
+    import ns3d_inputs as I
+    u0 = I.random_spectrum(N, seed=20240001)
+    out, states = {}, {}
+    for name, form in (("divergence", 0), ("advective", 1), ("rotational", 2)):
+        plan = B.Plan([N], B.NS3D_F32, eps0=1.0, cfl=0.5, nonlinear_form=form)
+        plan.set_initial(0, u0)
+        plan.step(2)
+        plan.synchronize()
+        plan.set_initial(0, u0)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        states[form] = plan.get_state(0).to(torch.complex128)
+        plan.close()
+        out[name] = {"ms_per_step": ms / steps, "value": N ** 3 * steps / (ms * 1e-3)}
+        if form:
+            d = torch.linalg.vector_norm(states[form] - states[0]) / torch.linalg.vector_norm(states[0])
+            out[name]["state_rel_l2_vs_divergence"] = float(d)
+    del states
+    torch.cuda.empty_cache()
+    return {"N": N, "steps": steps, "dtype": "f32", "unit": UNIT, **out}
+
+
 def embedded_ic(torch, N: int, cdtype, seed: int, k0: float, n0: int = 256):
     """The random-spectrum IC (E(k) ~ k^4 exp(-2 (k/k0)^2), E = 1/2) drawn on
     an n0^3 grid and embedded into the N^3 spectrum on the device: for k0 = 8
@@ -640,6 +672,7 @@ def main():
     if not args.no_extras and world == 1:
         line["batched_ensemble"] = bench_ensemble(B, torch, steps=10, warmup=2, to_t=1.0)
         line["plain_fp64"] = bench_plain_fp64(B, torch, N, steps=3)
+        line["nonlinear_forms"] = bench_forms(B, torch, N)
         line["largest"] = bench_largest(B, torch)
         line["cufft_pipeline"] = bench_cufft(torch, N)
         line["adjoint"] = bench_adjoint(B, torch)

@@ -75,8 +75,17 @@ typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
  *          environment variable NS3D_AUTOTUNE_CACHE, if set).  -1: the
  *          smallest such size without a benchmark.  > 0: that size (values
  *          below 3N/2 alias and are rejected).
- *   nonlinear_form: 0 = divergence form -i k.F[u (x) u] (the paper's; the only
- *          one the GPU path implements; 1 and 2 return NS3D_ERR_NOT_SUPPORTED).
+ *   nonlinear_form: the nonlinear term b before the Leray projection.
+ *          0 = divergence form -i k.F[u (x) u] (the paper's, section 2.3):
+ *          3 inverse and 6 forward transforms per evaluation, the fused FP32
+ *          kernels.  1 = advective form -F[(u . grad) u] from u and its nine
+ *          derivatives: 12 inverse and 3 forward.  2 = rotational form
+ *          F[u x curl u]: 6 inverse and 3 forward.  For a divergence-free
+ *          field with 3/2 padding the three agree after the projection up to
+ *          rounding.  Forms 1 and 2 run the generic tile kernels, take the
+ *          smallest 7-smooth padded size when n_pad = 0 (no benchmark), and
+ *          need more workspace (form 1: twice that of form 0).
+ *          ns3d_eval_rhs_noalloc takes form 0 only.
  *   dt_fixed > 0: fixed time step; otherwise dt = cfl * (L/N) / max_x sum_i |u_i|
  *          evaluated on the padded grid of the stage-1 field, per member. */
 typedef struct {
@@ -104,7 +113,9 @@ void ns3d_params_default(ns3d_params* p);
  * device.  workspace_limit_bytes: 0 = no limit; otherwise the plan fails with
  * NS3D_ERR_OUT_OF_MEMORY before allocating if it would need more.
  * Members start at u = 0, t = 0.  Errors: INVALID_ARG (sizes, params, null),
- * NOT_SUPPORTED (padded size not 7-smooth or nonlinear_form != 0),
+ * NOT_SUPPORTED (padded size not 7-smooth, or a form-1/2 z tile of one column
+ * that does not fit in shared memory: FP64 P > 1446 (form 1) or > 1808
+ * (form 2), FP32 P > 2854 (form 1) or > 3568 (form 2)),
  * OUT_OF_MEMORY, CUDA. */
 ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member, int batch, ns3d_dtype dtype,
                              const ns3d_params* p, void* cuda_stream,

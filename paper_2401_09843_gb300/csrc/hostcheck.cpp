@@ -22,6 +22,10 @@ namespace {
 // 2: as 1 but the three-pass kernels at the test factorisations below
 int g_use_fast = 1;
 
+// nonlinear form of the emulated right-hand side (0 divergence, 1 advective,
+// 2 rotational)
+int g_form = 0;
+
 // three-pass factorisations emulated at short lengths (the GPU builds them
 // for long lines only), so that their index logic meets the oracle
 #define NS3D_FOR_LONG_TEST(X) X(4, 3, 4) X(6, 4, 4) X(8, 4, 6) X(8, 6, 8)
@@ -127,6 +131,15 @@ void run_z(const ZArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   for (int z = 0; z < L.gz; ++z)
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < L.gx; ++x) zfused_block<T>(a, x, y, z, 0, 1, sm.data(), red, HostSync{});
+}
+
+template <typename T>
+void run_zform(const ZArgs<T>& a, int form, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
+  double red[1];
+  for (int z = 0; z < L.gz; ++z)
+    for (int y = 0; y < L.gy; ++y)
+      for (int x = 0; x < L.gx; ++x)
+        zform_block<T>(a, form, x, y, z, 0, 1, sm.data(), red, HostSync{});
 }
 
 // The register-resident z pass, phase by phase and thread by thread.
@@ -296,7 +309,7 @@ void run_xfused_prologue(const XFusedArgs<T>& a) {
 
 template <typename T>
 bool fused_shape(const ns3d::Geom& g) {
-  if (!g_use_fast || sizeof(T) != 4 || 3 * g.h != g.P) return false;
+  if (!g_use_fast || g.form != 0 || sizeof(T) != 4 || 3 * g.h != g.P) return false;
 #define NS3D_HC_XS(A, B) \
   if (g.P == (A) * (B)) return true;
   NS3D_FOR_XFUSED(NS3D_HC_XS)
@@ -345,6 +358,54 @@ void fused_stage(const ns3d::Geom& g, const SpecParams& sp, cplx<T>* u0, cplx<T>
 #undef NS3D_HC_XF
 }
 
+// rhs_stage for the advective and rotational forms (the plan's form path)
+template <typename T>
+void rhs_stage_form(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cplx<T>* u0,
+                    cplx<T>* us, cplx<T>* out, int stage, std::vector<cplx<T>>& W1,
+                    std::vector<cplx<T>>& W2, const std::vector<cplx<T>>& tw, Ns3dCtrl* ctrl,
+                    std::vector<cplx<T>>& sm) {
+  using namespace ns3d;
+  const long long N = g.N, P = g.P, h = g.h;
+  const int nf = form_fields(g.form);
+  for (long long i = 0; i < N * N * h; ++i)
+    form_prep_point<T>(in, W1.data(), g.N, T(sp.kscale), g.form, i);
+  Launch lx = launch_inv_x(g, 1);
+  lx.gz = nf;
+  run_col<T, +1, true, true>(args_inv_x<T>(g, W1.data(), W2.data(), tw.data()), lx, sm);
+  Launch ly = launch_inv_y(g, 1);
+  ly.gz = nf;
+  run_col<T, +1, true, true>(args_inv_y<T>(g, W2.data(), W1.data(), tw.data()), ly, sm);
+  ZArgs<T> az = args_z<T>(g, W1.data(), W2.data(), tw.data(), stage == 1 ? ctrl : nullptr);
+  az.W = g.Wzf;
+  az.ldw = g.ldwzf;
+  az.in_bs = nf * P * P * h;
+  az.out_bs = 3 * P * P * h;
+  run_zform<T>(az, g.form, Launch{cdiv(P, g.Wzf), g.P, 1, g.nthr_zf, g.smem_zf}, sm);
+  Launch lfy = launch_fwd_y(g, 1);
+  lfy.gz = 3;
+  run_col<T, -1, true, true>(args_fwd_y<T>(g, W2.data(), W1.data(), tw.data()), lfy, sm);
+  Launch lfx = launch_fwd_x(g, 1);
+  lfx.gz = 3;
+  run_col<T, -1, true, true>(args_fwd_x<T>(g, W1.data(), W2.data(), tw.data()), lfx, sm);
+  SpecArgs<T> s{};
+  s.bh = W2.data();
+  s.u0 = (stage == 0) ? in : u0;
+  s.us = us;
+  s.out = out;
+  s.N = g.N;
+  s.h = g.h;
+  s.nmem = 1;
+  s.stage = stage;
+  s.m6 = 3 * N * N * h;
+  s.m3 = g.nU;
+  s.sp = spec_t<T>(sp);
+  s.ctrl = ctrl;
+  s.form = g.form;
+  if (stage == 1) step_dt_member(*ctrl, sp);
+  for (int kx = 0; kx < g.N; ++kx)
+    for (int j = 0; j < g.N * g.h; ++j) spectral_point<T>(s, 0, kx, j);
+}
+
 // One evaluation of Algorithm 2 and the spectral step on member 0.
 template <typename T>
 void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cplx<T>* u0,
@@ -352,6 +413,10 @@ void rhs_stage(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in, cpl
                std::vector<cplx<T>>& W2, const std::vector<cplx<T>>& tw, Ns3dCtrl* ctrl,
                std::vector<cplx<T>>& sm) {
   using namespace ns3d;
+  if (g.form != 0) {
+    rhs_stage_form<T>(g, sp, in, u0, us, out, stage, W1, W2, tw, ctrl, sm);
+    return;
+  }
   run_col<T, +1, true, true>(args_inv_x<T>(g, in, W1.data(), tw.data()), launch_inv_x(g, 1), sm);
   run_col<T, +1, true, true>(args_inv_y<T>(g, W1.data(), W2.data(), tw.data()), launch_inv_y(g, 1), sm);
   {
@@ -382,13 +447,13 @@ template <typename T>
 int run(int N, int P, const double* prm, const void* uin, void* uout, int nsteps, double dt,
         double* t_out) {
   ns3d::Geom g;
-  if (!ns3d::make_geom(N, P, (int)sizeof(cplx<T>), &g)) return 1;
+  if (!ns3d::make_geom(N, P, (int)sizeof(cplx<T>), &g) || !ns3d::set_form_geom(&g, g_form)) return 1;
   // prm: L nu s theta eps0 mN_coef q_form cfl
   SpecParams sp = ns3d::make_spec_params(N, P, prm[0], prm[1], prm[2], prm[3], prm[4], prm[5],
                                          (int)prm[6], prm[7], dt);
   std::vector<cplx<T>> tw = ns3d::make_twiddles<T>(P);
   std::vector<cplx<T>> U0(g.nU), US(g.nU), W1(g.nW1), W2(g.nW2);
-  size_t sm_elems = std::max(g.smem_c, g.smem_z) / sizeof(cplx<T>) + 16;
+  size_t sm_elems = std::max(std::max(g.smem_c, g.smem_z), g.smem_zf) / sizeof(cplx<T>) + 16;
   std::vector<cplx<T>> sm(sm_elems);
   d1_to_compact((const cplx<T>*)uin, U0.data(), N);
   Ns3dCtrl ctrl{};
@@ -441,6 +506,9 @@ int ns3d_hostcheck_run(int dtype, int N, int P, const double* prm, const void* u
 
 // 0: emulate the generic tile z pass even where a register-resident one exists.
 void ns3d_hostcheck_use_fast(int mode) { g_use_fast = mode; }
+
+// nonlinear form of later ns3d_hostcheck_run calls (0, 1 or 2)
+void ns3d_hostcheck_set_form(int form) { g_form = form; }
 
 // One column pass of the three-pass kernel at P = 1536 (N = 1024) on a
 // [rows][ncols] array: sign > 0 the padded inverse (N rows in, P out),

@@ -241,6 +241,38 @@ struct ZLoadProd {
   }
 };
 
+// CFL maximum of one tile: max over its points of sum_i |u_i| (`get` gives the
+// velocity at (column, position)) into the member's control word, or the
+// non-finite flag.
+template <typename T, class Get, class Sync>
+NS3D_HD void z_umax_reduce(Ns3dCtrl* ctrl, int P, int ncol, int tid, int nthr, double* red,
+                           const Get& ph, const Sync& sync) {
+  T m = T(0);
+  int bad = 0;
+  for (int w = tid; w < P * ncol; w += nthr) {
+    const int col = w % ncol, p = w / ncol;
+    T u0, u1, u2;
+    ph.get(col, p, u0, u1, u2);
+    const T s = xabs(u0) + xabs(u1) + xabs(u2);
+    if (!(s <= big_finite<T>())) bad = 1;
+    else m = s > m ? s : m;
+  }
+  T* tred = reinterpret_cast<T*>(red);
+  tred[tid] = bad ? T(-1) : m;
+  sync();
+  if (tid == 0) {
+    T mm = T(0);
+    int anybad = 0;
+    for (int i = 0; i < nthr; ++i) {
+      const T r = tred[i];
+      anybad |= r < T(0);
+      mm = r > mm ? r : mm;
+    }
+    atomic_max_u64(&ctrl->umax_bits, dbl_bits((double)mm));
+    if (anybad) atomic_or_i32(&ctrl->status, NS3D_FLAG_NONFINITE);
+  }
+}
+
 template <typename T, class Sync>
 NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
                           cplx<T>* sm, double* red, const Sync& sync) {
@@ -265,32 +297,7 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
   sync();
 
   ZPhys<T> ph{U01, U2, ldw, half};
-  if (a.ctrl) {
-    T m = T(0);
-    int bad = 0;
-    for (int w = tid; w < P * ncol; w += nthr) {
-      const int col = w % ncol, p = w / ncol;
-      T u0, u1, u2;
-      ph.get(col, p, u0, u1, u2);
-      const T s = xabs(u0) + xabs(u1) + xabs(u2);
-      if (!(s <= big_finite<T>())) bad = 1;
-      else m = s > m ? s : m;
-    }
-    T* tred = reinterpret_cast<T*>(red);
-    tred[tid] = bad ? T(-1) : m;
-    sync();
-    if (tid == 0) {
-      T mm = T(0);
-      int anybad = 0;
-      for (int i = 0; i < nthr; ++i) {
-        const T r = tred[i];
-        anybad |= r < T(0);
-        mm = r > mm ? r : mm;
-      }
-      atomic_max_u64(&a.ctrl[bz].umax_bits, dbl_bits((double)mm));
-      if (anybad) atomic_or_i32(&a.ctrl[bz].status, NS3D_FLAG_NONFINITE);
-    }
-  }
+  if (a.ctrl) z_umax_reduce<T>(a.ctrl + bz, P, ncol, tid, nthr, red, ph, sync);
 
   // forward: three packed pairs of products, each truncated to kz < h
   cplx<T>* out = a.out + bz * a.out_bs + by * a.xs + (long long)y0 * h;
@@ -310,6 +317,189 @@ NS3D_HD void zfused_block(const ZArgs<T>& a, int bx, int by, int bz, int tid, in
       const cplx<T> d = zk - zm;
       oa[col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
       ob[col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);   // d / (2i)
+    }
+    sync();
+  }
+}
+
+// =====================================================================
+// The advective and rotational forms of the nonlinear term.  For a
+// divergence-free field with 3/2 padding both equal the divergence form after
+// the Leray projection, up to rounding:
+//   form 1  b = -F[(u . grad) u],   (u . grad) u_j = sum_l u_l d_l u_j
+//   form 2  b =  F[u x omega],      omega = curl u
+// (u x omega = -(u . grad) u + grad |u|^2 / 2, and a gradient projects out).
+// The fields taken to the padded grid: form 1 u_j and d_l u_j (field
+// 3 + 3 l + j), twelve; form 2 u_j and omega_j (field 3 + j), six.  The z pass
+// forms the three products in shared memory and returns them by two forward
+// transforms: (p0 + i p1) and p2.
+// =====================================================================
+
+NS3D_HDC int form_fields(int form) { return form == 1 ? 12 : (form == 2 ? 6 : 3); }
+
+// the spectral fields of one mode i of the compact [3][N][N][h] layout, into
+// F [nf][N][N][h]: u_hat itself, then i kappa_l u_hat_j (form 1) or
+// i kappa x u_hat (form 2)
+template <typename T>
+NS3D_HD void form_prep_point(const cplx<T>* u, cplx<T>* F, int N, T kscale, int form, long long i) {
+  const int h = N / 2;
+  const long long plane = (long long)N * N * h;
+  const int kz = (int)(i % h);
+  const int ky = (int)((i / h) % N), kx = (int)(i / ((long long)h * N));
+  const T k0 = kscale * T(kx < h ? kx : kx - N), k1 = kscale * T(ky < h ? ky : ky - N),
+          k2 = kscale * T(kz);
+  const cplx<T> v0 = u[i], v1 = u[plane + i], v2 = u[2 * plane + i];
+  F[i] = v0;
+  F[plane + i] = v1;
+  F[2 * plane + i] = v2;
+  if (form == 1) {
+    const T kl[3] = {k0, k1, k2};
+    const cplx<T> vj[3] = {v0, v1, v2};
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)   // i a (x + iy) = -a y + i a x
+        F[(3 + 3 * l + j) * plane + i] = cmake(-kl[l] * vj[j].y, kl[l] * vj[j].x);
+  } else {
+    const cplx<T> c0 = k1 * v2 - k2 * v1, c1 = k2 * v0 - k0 * v2, c2 = k0 * v1 - k1 * v0;
+    F[3 * plane + i] = cmake(-c0.y, c0.x);
+    F[4 * plane + i] = cmake(-c1.y, c1.x);
+    F[5 * plane + i] = cmake(-c2.y, c2.x);
+  }
+}
+
+// Inverse transforms of the z pass, in order: the fields (a, b) packed as
+// a + i b, one pair per transform (form 1: six, form 2: three).
+NS3D_HD void form_pair(int form, int step, int* a, int* b) {
+  // form 1: (u0,u1) (u2,d0u0) (d1u0,d2u0) (d0u1,d1u1) (d2u1,d0u2) (d1u2,d2u2)
+  const int f1[12] = {0, 1, 2, 3, 6, 9, 4, 7, 10, 5, 8, 11};
+  // form 2: (u0,u1) (u2,w0) (w1,w2)
+  const int f2[6] = {0, 1, 2, 3, 4, 5};
+  *a = form == 1 ? f1[2 * step] : f2[2 * step];
+  *b = form == 1 ? f1[2 * step + 1] : f2[2 * step + 1];
+}
+
+// Last pass of each inverse transform: the value v = a + i b at (column,
+// position) goes into the product buffers.  U01 = u0 + i u1 throughout;
+// X = u2 + i (form 1: N2, form 2: w0); form 1's Y = N0 + i N1, with
+// N_j = sum_l u_l d_l u_j.  After the last step the products are
+// form 1: Y = N0 + i N1, X = N2; form 2: U01 = p0 + i p1, X = p2 (p = u x w).
+template <typename T>
+struct ZFormStore {
+  cplx<T>* U01;
+  cplx<T>* X;
+  cplx<T>* Y;
+  int ldw, form, step;
+  NS3D_HD void operator()(int col, int f, cplx<T> v) const {
+    const int o = f * ldw + col;
+    if (step == 0) {
+      U01[o] = v;
+      return;
+    }
+    const cplx<T> uu = U01[o];
+    const T u0 = uu.x, u1 = uu.y;
+    if (form == 2) {
+      if (step == 1) {
+        X[o] = v;
+        return;
+      }
+      const cplx<T> xw = X[o];
+      const T u2 = xw.x, w0 = xw.y, w1 = v.x, w2 = v.y;
+      U01[o] = cmake(u1 * w2 - u2 * w1, u2 * w0 - u0 * w2);
+      X[o] = cmake(u0 * w1 - u1 * w0, T(0));
+      return;
+    }
+    if (step == 1) {                        // (u2, d0 u0)
+      X[o] = cmake(v.x, T(0));
+      Y[o] = cmake(u0 * v.y, T(0));
+      return;
+    }
+    const cplx<T> xw = X[o];
+    const T u2 = xw.x;
+    cplx<T> y = Y[o];
+    if (step == 2) {                        // (d1 u0, d2 u0)
+      y.x += u1 * v.x + u2 * v.y;
+      Y[o] = y;
+    } else if (step == 3) {                 // (d0 u1, d1 u1)
+      y.y = u0 * v.x + u1 * v.y;
+      Y[o] = y;
+    } else if (step == 4) {                 // (d2 u1, d0 u2)
+      y.y += u2 * v.x;
+      Y[o] = y;
+      X[o] = cmake(u2, u0 * v.y);
+    } else {                                // (d1 u2, d2 u2): N2 done, u2 no longer needed
+      X[o] = cmake(xw.y + u1 * v.x + u2 * v.y, T(0));
+    }
+  }
+};
+
+template <typename T>
+struct ZFormPhys {  // velocity after the second inverse transform
+  const cplx<T>* U01;
+  const cplx<T>* X;
+  int ldw;
+  NS3D_HD void get(int col, int p, T& u0, T& u1, T& u2) const {
+    const cplx<T> z = U01[p * ldw + col];
+    u0 = z.x;
+    u1 = z.y;
+    u2 = X[p * ldw + col].x;
+  }
+};
+
+// Shared elements of a zform tile: the product buffers (form 1: U01, X, Y;
+// form 2: U01, X) and the two transform buffers, P (W + 1) elements each.
+NS3D_HDC int zform_buffers(int form) { return form == 1 ? 5 : 4; }
+
+// z pass of forms 1 and 2 for one tile of W y columns at (member bz, x = by):
+// in [m][nf][P][P][h] (the inverse x and y of the form's fields), out
+// [m][3][P][P][h] the truncated half spectra of the three products.
+template <typename T, class Sync>
+NS3D_HD void zform_block(const ZArgs<T>& a, int form, int bx, int by, int bz, int tid, int nthr,
+                         cplx<T>* sm, double* red, const Sync& sync) {
+  const int P = a.P, h = a.h, W = a.W, ldw = a.ldw;
+  const int y0 = bx * W;
+  const int ncol = imin(W, P - y0);
+  const int nprod = form == 1 ? 3 : 2;
+  cplx<T>* U01 = sm;
+  cplx<T>* X = sm + P * ldw;
+  cplx<T>* Y = sm + 2 * P * ldw;            // form 1 only
+  cplx<T>* A = sm + nprod * P * ldw;
+  cplx<T>* B = A + P * ldw;
+  const cplx<T>* in = a.in + bz * a.in_bs + by * a.xs + (long long)y0 * h;
+  const int nsteps = form == 1 ? 6 : 3;
+  for (int st = 0; st < nsteps; ++st) {
+    int fa, fb;
+    form_pair(form, st, &fa, &fb);
+    ZLoadInvCols<T> ld{in + fa * a.in_cs, in + fb * a.in_cs, P, h, ncol, 0};
+    ZFormStore<T> sto{U01, X, Y, ldw, form, st};
+    fft_tile<T, +1, false, true>(a.pl, ncol, tid, nthr, a.tw, ld, sto, A, B, ldw, sync);
+    sync();
+    if (st == 1 && a.ctrl) {
+      ZFormPhys<T> ph{U01, X, ldw};
+      z_umax_reduce<T>(a.ctrl + bz, P, ncol, tid, nthr, red, ph, sync);
+      sync();
+    }
+  }
+  // forward: (p0 + i p1) untangled into two half spectra, then p2 alone
+  cplx<T>* out = a.out + bz * a.out_bs + by * a.xs + (long long)y0 * h;
+  for (int pair = 0; pair < 2; ++pair) {
+    SmemIO<T> src{pair == 0 ? (form == 1 ? Y : U01) : X, ldw};
+    cplx<T>* E = fft_free_buffer(a.pl.npass, A, B);
+    SmemIO<T> e{E, ldw};
+    fft_tile<T, -1, true, true>(a.pl, ncol, tid, nthr, a.tw, src, e, A, B, ldw, sync);
+    sync();
+    cplx<T>* oa = out + (2 * pair) * a.out_cs;
+    cplx<T>* ob = out + (2 * pair + 1) * a.out_cs;
+    for (int w = tid; w < h * ncol; w += nthr) {
+      const int k = w % h, col = w / h;
+      const cplx<T> zk = E[k * ldw + col];
+      const cplx<T> zm = cconj(E[((P - k) % P) * ldw + col]);
+      const cplx<T> s = zk + zm;
+      oa[col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
+      if (pair == 0) {
+        const cplx<T> d = zk - zm;
+        ob[col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);   // d / (2i)
+      }
     }
     sync();
   }
@@ -399,6 +589,7 @@ struct SpecArgs {
   SpecT<T> sp;         // parameters in the arithmetic type
   Ns3dCtrl* ctrl;
   const T* lam;        // lambda_k by integer |k|^2 (evaluated in FP64 once), or null
+  int form;            // 0: bh = F[u_j u_l] (6); 1: bh = F[(u.grad)u], 2: bh = F[u x omega] (3)
 };
 
 template <typename T> NS3D_HD T ctrl_dt(const Ns3dCtrl& c);
@@ -438,14 +629,22 @@ NS3D_HD void spectral_point(const SpecArgs<T>& a, int m, int kx, int j) {
   } else {
     const cplx<T>* bh = a.bh + m * a.m6 + off;
     const T kx_ = sp.kscale * T(sx), ky_ = sp.kscale * T(sy), kz_ = sp.kscale * T(kz);
-    cplx<T> b6[6];
-    for (int q = 0; q < 6; ++q) b6[q] = sp.inv_P3 * bh[q * plane];
-    // kappa . B_j  (B symmetric: 00 01 02 11 12 22)
-    const cplx<T> t0 = kx_ * b6[0] + ky_ * b6[1] + kz_ * b6[2];
-    const cplx<T> t1 = kx_ * b6[1] + ky_ * b6[3] + kz_ * b6[4];
-    const cplx<T> t2 = kx_ * b6[2] + ky_ * b6[4] + kz_ * b6[5];
-    // b = -i t
-    const cplx<T> bb[3] = {cmake(t0.y, -t0.x), cmake(t1.y, -t1.x), cmake(t2.y, -t2.x)};
+    cplx<T> bb[3];
+    if (a.form == 0) {
+      cplx<T> b6[6];
+      for (int q = 0; q < 6; ++q) b6[q] = sp.inv_P3 * bh[q * plane];
+      // kappa . B_j  (B symmetric: 00 01 02 11 12 22)
+      const cplx<T> t0 = kx_ * b6[0] + ky_ * b6[1] + kz_ * b6[2];
+      const cplx<T> t1 = kx_ * b6[1] + ky_ * b6[3] + kz_ * b6[4];
+      const cplx<T> t2 = kx_ * b6[2] + ky_ * b6[4] + kz_ * b6[5];
+      // b = -i t
+      bb[0] = cmake(t0.y, -t0.x);
+      bb[1] = cmake(t1.y, -t1.x);
+      bb[2] = cmake(t2.y, -t2.x);
+    } else {
+      const T sg = a.form == 1 ? -sp.inv_P3 : sp.inv_P3;
+      for (int q = 0; q < 3; ++q) bb[q] = sg * bh[q * plane];
+    }
     const T kap2 = kx_ * kx_ + ky_ * ky_ + kz_ * kz_;
     const cplx<T> kb = (T(1) / kap2) * (kx_ * bb[0] + ky_ * bb[1] + kz_ * bb[2]);
     const T lam = a.lam ? a.lam[k2] : lambda_k<T>(k2, sp);

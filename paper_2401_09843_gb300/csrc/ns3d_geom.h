@@ -68,6 +68,9 @@ struct Geom {
   size_t smem_cN = 0;
   int Wz = 0, ldwz = 0, nthr_z = 128;   // fused z pass
   size_t smem_z = 0;
+  int form = 0;                          // nonlinear form (0 divergence, 1 advective, 2 rotational)
+  int Wzf = 0, ldwzf = 0, nthr_zf = 128; // z pass of forms 1 and 2
+  size_t smem_zf = 0;
 };
 
 constexpr size_t kSmemTarget = 113 * 1024;   // two blocks per SM
@@ -119,6 +122,33 @@ inline bool make_geom(int N, int P, int esz, Geom* g) {
   g->Wz = Wz;
   g->ldwz = Wz + 1;
   g->smem_z = needz(Wz);
+  return true;
+}
+
+// Forms 1 and 2 of the nonlinear term: workspaces for the form's nf fields
+// (W1: nf P^2 h after the inverse y pass; W2: nf P N h after the inverse x
+// pass, 3 P^2 h after the z pass) and the zform_block tile (W y columns,
+// zform_buffers(form) shared lines of P (W + 1) elements).
+inline bool set_form_geom(Geom* g, int form) {
+  g->form = form;
+  if (form == 0) return true;
+  const long long n = g->N, p = g->P, h = g->h;
+  const long long nf = form_fields(form);
+  g->nW1 = std::max(g->nW1, nf * p * p * h);
+  g->nW2 = std::max(g->nW2, std::max(nf * p * n * h, 3 * p * p * h));
+  const int nb = zform_buffers(form);
+  auto need = [&](int w, int nthr) {
+    return (size_t)nb * g->P * (w + 1) * g->esz + (size_t)8 * nthr;
+  };
+  int W = g->esz == 8 ? 4 : 8;
+  while (W > 1 && need(W, 128) > kSmemTarget) W /= 2;
+  // one block per SM anyway: FP32 runs 512 threads instead of 128
+  const int nthr = (g->esz == 8 && need(W, 128) > kSmemTarget) ? 512 : 128;
+  if (need(W, nthr) > kSmemMax) return false;
+  g->Wzf = W;
+  g->ldwzf = W + 1;
+  g->nthr_zf = nthr;
+  g->smem_zf = need(W, nthr);
   return true;
 }
 

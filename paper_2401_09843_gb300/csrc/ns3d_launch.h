@@ -173,6 +173,14 @@ template <typename T>
 cudaError_t zfused_init();
 template <typename T>
 cudaError_t launch_spectral(const SpecArgs<T>& a, cudaStream_t s);
+// nonlinear forms 1 and 2: the form's spectral fields, and the z pass with products
+template <typename T>
+cudaError_t launch_form_prep(const cplx<T>* u, cplx<T>* F, int N, T kscale, int form, long long mu,
+                             long long mf, int nm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zform(const ZArgs<T>& a, int form, const Launch& L, cudaStream_t s);
+template <typename T>
+cudaError_t zform_init();
 // per-member time step of the step starting now (before the stage-1 spectral kernel)
 cudaError_t launch_step_dt(Ns3dCtrl* c, int n, const SpecParams& sp, cudaStream_t s);
 template <typename T>
@@ -182,8 +190,8 @@ cudaError_t launch_compact_to_d1(const cplx<T>* u, cplx<T>* d1, int N, cudaStrea
 
 template <typename T>
 cudaError_t kernels_init() {
-  cudaError_t e[3] = {col_init<T, +1, true, true>(), col_init<T, -1, true, true>(),
-                      zfused_init<T>()};
+  cudaError_t e[4] = {col_init<T, +1, true, true>(), col_init<T, -1, true, true>(),
+                      zfused_init<T>(), zform_init<T>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   if (sizeof(T) == 8) {

@@ -241,6 +241,69 @@ ns3d_status ensure_prologue(ns3d_plan p) {
 
 }  // namespace
 
+namespace {
+
+// enqueue_rhs for the advective (1) and rotational (2) forms: the form's nf
+// spectral fields, their inverse x and y passes, the z pass that forms the
+// three products, forward y and x of the products and the spectral step with
+// b taken as it is (no kappa contraction).
+template <typename T>
+ns3d_status enqueue_rhs_form(const StageBufs& b, int stage, int nm, const cplx<T>* in,
+                             cplx<T>* out, bool want_umax, cudaStream_t s, KernelTimer* tm) {
+  const Geom& g = *b.g;
+  const long long N = g.N, P = g.P, h = g.h;
+  const int nf = form_fields(g.form);
+  cplx<T>* W1 = static_cast<cplx<T>*>(b.W1);
+  cplx<T>* W2 = static_cast<cplx<T>*>(b.W2);
+  const cplx<T>* tw = static_cast<const cplx<T>*>(b.tw);
+  NS3D_MARK(0);
+  NS3D_CK(launch_form_prep<T>(in, W1, g.N, T(b.sp.kscale), g.form, g.nU, nf * N * N * h, nm, s));
+  Launch lx = launch_inv_x(g, nm);
+  lx.gz = nm * nf;
+  NS3D_CK(launch_col<T>(args_inv_x<T>(g, W1, W2, tw), COL_INV_CC, lx, s));
+  NS3D_MARK(1);
+  Launch ly = launch_inv_y(g, nm);
+  ly.gz = nm * nf;
+  NS3D_CK(launch_col<T>(args_inv_y<T>(g, W2, W1, tw), COL_INV_CC, ly, s));
+  NS3D_MARK(2);
+  ZArgs<T> az = args_z<T>(g, W1, W2, tw, want_umax ? b.ctrl : nullptr);
+  az.W = g.Wzf;
+  az.ldw = g.ldwzf;
+  az.in_bs = nf * P * P * h;
+  az.out_bs = 3 * P * P * h;
+  NS3D_CK(launch_zform<T>(az, g.form, Launch{cdiv(P, g.Wzf), g.P, nm, g.nthr_zf, g.smem_zf}, s));
+  NS3D_MARK(3);
+  Launch lfy = launch_fwd_y(g, nm);
+  lfy.gz = nm * 3;
+  NS3D_CK(launch_col<T>(args_fwd_y<T>(g, W2, W1, tw), COL_FWD_CC, lfy, s));
+  NS3D_MARK(4);
+  Launch lfx = launch_fwd_x(g, nm);
+  lfx.gz = nm * 3;
+  NS3D_CK(launch_col<T>(args_fwd_x<T>(g, W1, W2, tw), COL_FWD_CC, lfx, s));
+  NS3D_MARK(5);
+  SpecArgs<T> a{};
+  a.bh = W2;
+  a.u0 = (stage == 0) ? in : static_cast<cplx<T>*>(b.u0);
+  a.us = static_cast<cplx<T>*>(b.us);
+  a.out = out;
+  a.N = g.N;
+  a.h = g.h;
+  a.nmem = nm;
+  a.stage = stage;
+  a.m6 = 3 * N * N * h;
+  a.m3 = g.nU;
+  a.sp = spec_t<T>(b.sp);
+  a.ctrl = b.ctrl;
+  a.lam = static_cast<const T*>(b.lam);
+  a.form = g.form;
+  if (stage == 1) NS3D_CK(launch_step_dt(b.ctrl, nm, b.sp, s));
+  NS3D_CK(launch_spectral<T>(a, s));
+  NS3D_MARK(6);
+  return NS3D_OK;
+}
+
+}  // namespace
+
 // One evaluation of Algorithm 2 plus the spectral step for members [0, nm)
 // of the buffers.  `in` is the field R is evaluated at; stage 0 writes R to
 // `out`, stages 1-3 the SSP-RK3 combinations.
@@ -248,6 +311,7 @@ template <typename T>
 ns3d_status enqueue_rhs(const StageBufs& b, int stage, int nm, const cplx<T>* in, cplx<T>* out,
                         bool want_umax, cudaStream_t s, KernelTimer* tm) {
   const Geom& g = *b.g;
+  if (g.form != 0) return enqueue_rhs_form<T>(b, stage, nm, in, out, want_umax, s, tm);
   cplx<T>* W1 = static_cast<cplx<T>*>(b.W1);
   cplx<T>* W2 = static_cast<cplx<T>*>(b.W2);
   const cplx<T>* tw = static_cast<const cplx<T>*>(b.tw);
@@ -519,7 +583,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
       !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < -1 ||
       !(P.dt_fixed >= 0) || (P.dt_fixed == 0 && !(P.cfl > 0)))
     return NS3D_ERR_INVALID_ARG;
-  if (P.nonlinear_form != 0) return NS3D_ERR_NOT_SUPPORTED;
+  if (P.nonlinear_form < 0 || P.nonlinear_form > 2) return NS3D_ERR_INVALID_ARG;
   std::map<int, std::vector<int>> byN;
   for (int i = 0; i < batch; ++i) {
     const int N = N_per_member[i];
@@ -542,17 +606,21 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     if (P.n_pad > 0) {
       if (2 * P.n_pad < 3 * L.N) { delete p; return NS3D_ERR_INVALID_ARG; }
       L.P = P.n_pad;
-    } else if (P.n_pad == 0) {
+    } else if (P.n_pad == 0 && P.nonlinear_form == 0) {
       if (dtype == NS3D_F32) kernels_init<float>();
       else kernels_init<double>();
       L.P = autotune_padded_size(L.N, dtype, P, p->stream);
     } else {
       L.P = default_padded_size(L.N);
     }
-    if (!make_geom(L.N, L.P, p->esz, &L.g)) { delete p; return NS3D_ERR_NOT_SUPPORTED; }
+    if (!make_geom(L.N, L.P, p->esz, &L.g) || !set_form_geom(&L.g, P.nonlinear_form)) {
+      delete p;
+      return NS3D_ERR_NOT_SUPPORTED;
+    }
     L.sp = make_spec_params(L.N, L.P, P.L, P.nu, P.s, P.theta, P.eps0, P.mN_coef, P.q_form, P.cfl,
                             P.dt_fixed);
-    L.fused = dtype == NS3D_F32 ? xfused_available<float>(L.g) : xfused_available<double>(L.g);
+    L.fused = P.nonlinear_form == 0 &&
+              (dtype == NS3D_F32 ? xfused_available<float>(L.g) : xfused_available<double>(L.g));
     const Geom& g = L.g;
     need += (size_t)L.B * (2 * g.nU + g.nW1 + g.nW2) * p->esz + (size_t)L.P * p->esz +
             (size_t)L.B * sizeof(Ns3dCtrl);
@@ -607,7 +675,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
   }
   p->staging_bytes = stag;
   p->launches_per_step = 0;
-  for (const Level& L : p->levels) p->launches_per_step += L.fused ? 13 : 19;
+  for (const Level& L : p->levels) p->launches_per_step += L.g.form ? 22 : (L.fused ? 13 : 19);
   *out = p;
   return NS3D_OK;
 }

@@ -68,8 +68,9 @@ def test_invalid_arguments_are_rejected(built):
         assert lib.ns3d_plan_create(ctypes.byref(h), arr, 1, 0, ctypes.byref(p), None, 0) == 1
     assert lib.ns3d_plan_create(ctypes.byref(h), ok, 0, 0, ctypes.byref(p), None, 0) == 1
     assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 5, ctypes.byref(p), None, 0) == 1
-    q = binding.default_params(nonlinear_form=1)
-    assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 7
+    for form in (-1, 3):                               # 0, 1 and 2 are the three forms
+        q = binding.default_params(nonlinear_form=form)
+        assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 1
     q = binding.default_params(n_pad=40)              # below 3N/2 = 48: would alias
     assert lib.ns3d_plan_create(ctypes.byref(h), ok, 1, 0, ctypes.byref(q), None, 0) == 1
     q = binding.default_params(cfl=0.0)
@@ -135,6 +136,33 @@ def test_emulated_kernels_steps_match_oracle(built):
     ref, tref, _ = S.integrate(uh, prm, 2, P=P)
     got, rc, t = hostcheck(built, uh, P, prm, nsteps=2, dt=0.0)
     assert abs(t - tref) < 1e-14 and rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("N,P", [(8, 12), (10, 15), (16, 24), (22, 35), (32, 48), (24, 40)])
+def test_emulated_nonlinear_forms_match_oracle(built, form, N, P):
+    """The advective (1) and rotational (2) form paths of the kernels: the
+    form's fields, their inverse passes, the z pass forming the products in
+    shared memory, the forward passes and the spectral step, against the
+    oracle's form and against the divergence form (equal after projection)."""
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_set_form(form)
+    try:
+        prm = S.Params(nu=0.01, eps0=1.0, L=5.0, nonlinear_form=form)
+        uh = I.random_spectrum(N, seed=N + 7 * form, k0=2.5)
+        ref = S.rhs(uh, prm, P=P)
+        got, rc, _ = hostcheck(built, uh, P, prm)
+        assert rc == 0
+        assert rel(got, ref) < 1e-13
+        assert rel(got, S.rhs(uh, prm, P=P, form=0)) < 1e-13
+        got32, _, _ = hostcheck(built, uh, P, prm, dtype=0)
+        assert rel(got32, ref) < 2e-6
+        if N == 16:   # CFL steps: the same dt sequence as the oracle's
+            ref, tref, _ = S.integrate(uh, prm, 2, P=P)
+            got, rc, t = hostcheck(built, uh, P, prm, nsteps=2, dt=0.0)
+            assert rc == 0 and abs(t - tref) < 1e-14 and rel(got, ref) < 1e-12
+    finally:
+        lib.ns3d_hostcheck_set_form(0)
 
 
 def test_radix_plans(built):
