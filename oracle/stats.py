@@ -16,6 +16,9 @@ formulas for them; the definitions used (both here and in the library) are:
 * structure function    S2(r)     = (1/3) sum_d <|u(x + r e_d) - u(x)|^2>_x
                                   = (1/3) sum_d sum_k 2 |u_hat_k|^2 (1 - cos(kappa_d r)),
                         r = j L / N, j = 1 .. N/2
+* ball-averaged S2      S2_ball(r) = < (1/|B_r|) int_{|h|<=r} |u(x+h) - u(x)|^2 dh >_x
+                                  = sum_k 2 |u_hat_k|^2 (1 - 3 (sin q - q cos q) / q^3),
+                        q = |kappa| r, at the same r
 * enstrophy spectrum    Z(K)      = 1/2 sum_{k : round(|k|) = K} |omega_hat_k|^2,
                         omega_hat = i kappa x u_hat (the vorticity the paper's
                         section 6.1 shows, as a spectrum writer)
@@ -77,6 +80,39 @@ def structure_function_spectral(uhat: np.ndarray, L: float) -> np.ndarray:
     return out
 
 
+def one_minus_ball_mean_cos(q):
+    """1 - j(q), j(q) = (1/|B_r|) int_{|h| <= r} cos(kappa . h) dh = 3 (sin q - q cos q) / q^3
+    with q = |kappa| r (the ball's indicator in Fourier space; j(0) = 1).
+
+    For q < 1 the difference is summed from the Taylor series of
+    sin q - q cos q = sum_{n >= 1} (-1)^(n+1) 2n q^(2n+1) / (2n+1)!, which gives
+    1 - j(q) = sum_{n >= 2} (-1)^n 6n q^(2n-2) / (2n+1)!  (the direct formula
+    cancels there); 14 terms leave less than 1e-28."""
+    q = np.asarray(q, dtype=np.float64)
+    small = q < 1.0
+    qs = np.where(small, q, 0.0)
+    series = np.zeros_like(q)
+    for n in range(2, 16):
+        series += (-1) ** n * 6 * n / math.factorial(2 * n + 1) * qs ** (2 * n - 2)
+    ql = np.where(small, 1.0, q)
+    direct = 1.0 - 3.0 * (np.sin(ql) - ql * np.cos(ql)) / ql ** 3
+    return np.where(small, series, direct)
+
+
+def structure_function_ball(uhat: np.ndarray, L: float, r=None) -> np.ndarray:
+    """Ball-averaged second-order structure function
+        S2_ball(r) = < (1/|B_r|) int_{|h| <= r} |u(x + h) - u(x)|^2 dh >_x
+                   = sum_k |u_hat_k|^2 2 (1 - j(|kappa| r))          (full spectrum),
+    by default at r = j L / N, j = 1 .. N/2.  The axis-lag S2 above averages the
+    increment over the three axis directions instead of the ball."""
+    N = uhat.shape[-2]
+    kx, ky, kz = wavenumbers(N)
+    kap = (2 * math.pi / L) * np.sqrt((kx ** 2 + ky ** 2 + kz ** 2).astype(np.float64))
+    e = np.sum(np.abs(uhat) ** 2, axis=0) * half_weights(N)
+    rs = np.arange(1, N // 2 + 1) * L / N if r is None else np.atleast_1d(np.asarray(r, float))
+    return np.array([np.sum(e * 2.0 * one_minus_ball_mean_cos(kap * rr)) for rr in rs])
+
+
 def structure_function_brute(u: np.ndarray) -> np.ndarray:
     """S2 from grid values by shifting whole grid points (r = j L / N)."""
     N = u.shape[-1]
@@ -132,13 +168,14 @@ def ensemble_stats(uhats: np.ndarray, L: float, prm=None) -> dict:
     en = spec.sum(axis=1)
     spec_m, spec_se = mean_and_stderr(spec)
     s2_m, s2_se = mean_and_stderr(s2)
+    s2b_m, s2b_se = mean_and_stderr(np.stack([structure_function_ball(u, L) for u in uhats]))
     en_m, en_se = mean_and_stderr(en)
     zspec = np.stack([enstrophy_spectrum(u, L) for u in uhats])
     zs_m, zs_se = mean_and_stderr(zspec)
     z_m, z_se = mean_and_stderr(zspec.sum(axis=1))
     out = dict(M=M, N=N, mean=mean, second=second, var=var,
                spectrum=spec_m, spectrum_stderr=spec_se,
-               s2=s2_m, s2_stderr=s2_se,
+               s2=s2_m, s2_stderr=s2_se, s2_ball=s2b_m, s2_ball_stderr=s2b_se,
                energy=float(en_m), energy_stderr=float(en_se),
                enstrophy_spectrum=zs_m, enstrophy_spectrum_stderr=zs_se,
                enstrophy=float(z_m), enstrophy_stderr=float(z_se))

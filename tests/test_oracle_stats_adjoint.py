@@ -31,6 +31,53 @@ def test_structure_function_spectral_equals_brute_force(N, L):
                        rtol=1e-12, atol=1e-15)
 
 
+def test_ball_mean_cos_against_quadrature():
+    """j(q) = average of cos(kappa . h) over the ball |h| <= r, by Gauss-Legendre
+    quadrature in spherical coordinates with kappa off the axes."""
+    xr, wr = np.polynomial.legendre.leggauss(40)
+    xt, wt = np.polynomial.legendre.leggauss(40)
+    nphi = 96
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    rho = 0.5 * (xr + 1.0)                           # r = 1, rho in (0, 1)
+    mu = xt                                          # cos(theta)
+    R, MU, PH = np.meshgrid(rho, mu, phi, indexing="ij")
+    W = (0.5 * wr)[:, None, None] * wt[None, :, None] * (2 * np.pi / nphi)
+    st = np.sqrt(1.0 - MU ** 2)
+    h = np.stack([R * st * np.cos(PH), R * st * np.sin(PH), R * MU])
+    d = np.array([1.0, -2.0, 2.0]) / 3.0
+    for q in (0.05, 0.7, 1.0, 2.5, 7.0):
+        kap = q * d
+        f = np.cos(np.tensordot(kap, h, axes=1)) * R ** 2
+        avg = np.sum(W * f) / (4.0 * np.pi / 3.0)
+        assert abs((1.0 - avg) - T.one_minus_ball_mean_cos(q)) < 1e-13 * max(1.0, 1.0 - avg), q
+    # both branches meet at q = 1
+    a = T.one_minus_ball_mean_cos(np.nextafter(1.0, 0.0))
+    b = T.one_minus_ball_mean_cos(1.0)
+    assert abs(a - b) < 1e-15
+
+
+def test_ball_structure_function_pins():
+    L = 2 * math.pi
+    N = 16
+    u = I.random_spectrum(N, seed=9, k0=3.0)
+    # small r: 2 (1 - j(q)) ~ q^2 / 5, so S2_ball(r) / r^2 -> (1/5) sum |kappa|^2 |u_hat|^2 = 2 Z / 5
+    Z = float(np.sum(T.enstrophy_spectrum(u, L)))
+    r = 1e-4
+    assert abs(T.structure_function_ball(u, L, r)[0] / r ** 2 - 0.4 * Z) < 1e-6 * Z
+    # large r: j -> 0, S2_ball -> 2 sum |u_hat|^2 = 4 E for a field without mean flow
+    E = float(np.sum(T.energy_spectrum(u)))
+    assert abs(T.structure_function_ball(u, L, 1e8)[0] - 4 * E) < 1e-12 * E
+    # one mode u = (0, sin 3x, 0): |sin 3(x + h_x) - sin 3x|^2 averages over x to
+    # 1 - cos 3 h_x, and over the ball to 1 - j(3 r)
+    one = np.zeros((3, N, N, N // 2 + 1), complex)
+    one[1, 3, 0, 0] = -0.5j
+    one[1, N - 3, 0, 0] = 0.5j
+    rs = np.arange(1, N // 2 + 1) * L / N
+    got = T.structure_function_ball(one, L)
+    j = 3 * (np.sin(3 * rs) - 3 * rs * np.cos(3 * rs)) / (3 * rs) ** 3
+    assert np.max(np.abs(got - (1.0 - j))) < 1e-14
+
+
 def test_identical_samples_have_zero_variance_and_exact_moments():
     uh = I.random_spectrum(8, seed=1)
     st = T.ensemble_stats(np.stack([uh] * 4), TWO_PI)
