@@ -206,7 +206,15 @@ ns3d_status ns3d_grad_band_energy(ns3d_plan plan, int member, double k_lo, doubl
  *   dissipation, dissipation_se of D = sum_k lambda_k |u_hat_k|^2 over the full
  *                               spectrum: the exact energy loss rate -dE/dt of
  *                               the semi-discrete system (the dealiased
- *                               nonlinear term conserves E) */
+ *                               nonlinear term conserves E)
+ *   s2_ball, s2_ball_se [N/2]   mean and standard error of the ball-averaged
+ *                               S2_ball(r) = < (1/|B_r|) int_{|h|<=r} |u(x+h) - u(x)|^2 dh >_x
+ *                               = sum_k |u_hat_k|^2 2 (1 - 3 (sin q - q cos q) / q^3),
+ *                               q = |kappa| r, r = jL/N (computed only when
+ *                               either pointer is non-NULL: N/2 passes over the
+ *                               coefficients)
+ * The spectra, S2 and D are compensated FP64 sums in a fixed order: two calls on
+ * the same state return the same bits. */
 typedef struct {
   double* mean;
   double* second;
@@ -224,6 +232,8 @@ typedef struct {
   double enstrophy_se;
   double dissipation;
   double dissipation_se;
+  double* s2_ball;
+  double* s2_ball_se;
 } ns3d_stats;
 
 ns3d_status ns3d_ensemble_stats(ns3d_plan plan, int level_N, ns3d_stats* out);

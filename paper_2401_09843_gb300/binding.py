@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("members", ctypes.c_int),
                 ("enstrophy_spectrum", ctypes.c_void_p), ("enstrophy_spectrum_se", ctypes.c_void_p),
                 ("enstrophy", ctypes.c_double), ("enstrophy_se", ctypes.c_double),
-                ("dissipation", ctypes.c_double), ("dissipation_se", ctypes.c_double)]
+                ("dissipation", ctypes.c_double), ("dissipation_se", ctypes.c_double),
+                ("s2_ball", ctypes.c_void_p), ("s2_ball_se", ctypes.c_void_p)]
 
 
 _lib = None
@@ -271,7 +272,7 @@ class Plan:
                "ns3d_grad_band_energy")
         return out
 
-    def ensemble_stats(self, level_N: int, fields: bool = True):
+    def ensemble_stats(self, level_N: int, fields: bool = True, ball: bool = True):
         N = int(level_N)
         res = {}
         arrays = {}
@@ -285,6 +286,9 @@ class Plan:
         arrays["s2_se"] = np.zeros(N // 2)
         arrays["enstrophy_spectrum"] = np.zeros(N)
         arrays["enstrophy_spectrum_se"] = np.zeros(N)
+        if ball:
+            arrays["s2_ball"] = np.zeros(N // 2)
+            arrays["s2_ball_se"] = np.zeros(N // 2)
         st = Stats()
         for k, v in arrays.items():
             setattr(st, k, v.ctypes.data_as(ctypes.c_void_p))

@@ -10,6 +10,7 @@
 // For the pointwise fields the member's velocity is taken to the N^3 grid
 // (unpadded inverse transforms: x, y column passes and a c2r z pass) and a
 // Welford update adds it to the pointwise mean and co-moments.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -138,15 +139,110 @@ __global__ void k_spectra(const cplx<T>* u, int N, double kscale2, SpecT<double>
   }
 }
 
-// hist[bin] = the planes' pairs merged in kx order, rounded once
-__global__ void k_spectra_merge(const double2* part, int N, int L, double* hist) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+// hist[i] = the planes' pairs part[kx][i] (row length L) merged in kx order,
+// rounded once, for i < nout
+__global__ void k_spectra_merge(const double2* part, int N, int L, int nout, double* hist) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nout; i += gridDim.x * blockDim.x) {
     CSum a{0.0, 0.0};
     for (int kx = 0; kx < N; ++kx) {
       const double2 q = part[(size_t)kx * L + i];
       a = csum_merge(a, CSum{q.x, q.y});
     }
     hist[i] = a.s + a.c;
+  }
+}
+
+// ---- ball-averaged structure function
+// S2_ball(r_j) = sum_k e_k 2 (1 - jb(q)), jb(q) = 3 (sin q - q cos q) / q^3,
+// q = |kappa| r_j = 2 pi j |k| / N (independent of L), e_k = |u_hat_k|^2 summed
+// over components and over the mirror mode.  The factor depends on |k|^2 only:
+// a table per radius, kBallJ radii per pass over the coefficients.
+
+constexpr int kBallJ = 16;
+
+// Taylor coefficients of 1 - jb(q) in t = q^2:
+//   1 - jb = t sum_{n=2}^{15} (-1)^n 6n / (2n+1)! t^(n-2)
+// (from sin q - q cos q = sum_{n>=1} (-1)^(n+1) 2n q^(2n+1) / (2n+1)!)
+struct BallCoef {
+  double c[14];
+};
+
+BallCoef ball_coefficients() {
+  BallCoef b{};
+  double f = 6.0;                                    // (2n+1)! at n = 1
+  for (int n = 2; n <= 15; ++n) {
+    f *= (double)(2 * n) * (double)(2 * n + 1);
+    b.c[n - 2] = ((n % 2) ? -6.0 : 6.0) * n / f;
+  }
+  return b;
+}
+
+// 1 - jb(q): the series (Horner in q^2) below q = 1, where the closed form
+// cancels; the closed form above
+__device__ double one_minus_jb(double q, const BallCoef& b) {
+  if (q < 1.0) {
+    const double t = q * q;
+    double acc = b.c[13];
+#pragma unroll
+    for (int n = 12; n >= 0; --n) acc = acc * t + b.c[n];
+    return t * acc;
+  }
+  return 1.0 - 3.0 * (sin(q) - q * cos(q)) / (q * q * q);
+}
+
+// G[jj][k2] = 2 (1 - jb(2 pi (j0 + jj) sqrt(k2) / N)), jj < nj, k2 < nk2
+__global__ void k_ball_table(double* G, int nk2, int j0, int nj, int N, BallCoef b) {
+  const double PI = 3.14159265358979323846;
+  const long long total = (long long)nj * nk2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int jj = (int)(i / nk2), k2 = (int)(i % nk2);
+    const double q = 2.0 * PI * (double)(j0 + jj) * sqrt((double)k2) / (double)N;
+    G[i] = 2.0 * one_minus_jb(q, b);
+  }
+}
+
+// One member, one block per kx plane, 256 threads: per radius jj < nj the
+// compensated sum over the plane's modes of e_k G[jj][|k|^2], merged over the
+// threads in a fixed order into part[kx][jj].
+template <typename T>
+__global__ void __launch_bounds__(256) k_s2_ball(const cplx<T>* u, int N, const double* G, int nk2,
+                                                 int nj, double2* part) {
+  __shared__ double2 sh[8][kBallJ];
+  const int h = N / 2;
+  const int kx = blockIdx.x;
+  const int sx = kx < h ? kx : kx - N;
+  const long long plane = (long long)N * N * h;
+  CSum acc[kBallJ];
+#pragma unroll
+  for (int jj = 0; jj < kBallJ; ++jj) acc[jj] = CSum{0.0, 0.0};
+  for (int i = threadIdx.x; i < N * h; i += blockDim.x) {
+    const int ky = i / h, kz = i % h;
+    const long long off = (long long)kx * N * h + i;
+    double e = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> v = u[c * plane + off];
+      e += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    if (kz > 0) e *= 2.0;
+    const int sy = ky < h ? ky : ky - N;
+    const int k2 = sx * sx + sy * sy + kz * kz;
+#pragma unroll
+    for (int jj = 0; jj < kBallJ; ++jj)
+      if (jj < nj) acc[jj] = csum_merge(acc[jj], CSum{e * G[(size_t)jj * nk2 + k2], 0.0});
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int jj = 0; jj < kBallJ; ++jj) {
+    const CSum w = csum_warp(acc[jj]);
+    if (lane == 0) sh[warp][jj] = make_double2(w.s, w.c);
+  }
+  __syncthreads();
+  if (threadIdx.x < nj) {
+    CSum a{0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+      a = csum_merge(a, CSum{sh[w][threadIdx.x].x, sh[w][threadIdx.x].y});
+    part[(size_t)kx * kBallJ + threadIdx.x] = make_double2(a.s, a.c);
   }
 }
 
@@ -229,6 +325,20 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
   if (nws < 1) return NS3D_ERR_NOT_SUPPORTED;
   double* hist = static_cast<double*>(alloc(sizeof(double) * HL * M));
   double2* part = static_cast<double2*>(alloc(sizeof(double2) * HL * (size_t)N));
+  const bool ball = out->s2_ball || out->s2_ball_se;
+  const int nk2 = 2 * h * h + (h - 1) * (h - 1) + 1;   // |k|^2 <= h^2 + h^2 + (h - 1)^2
+  double* G = nullptr;
+  double2* partb = nullptr;
+  double* s2b = nullptr;
+  if (ball) {
+    G = static_cast<double*>(alloc(sizeof(double) * kBallJ * (size_t)nk2));
+    partb = static_cast<double2*>(alloc(sizeof(double2) * kBallJ * (size_t)N));
+    s2b = static_cast<double*>(alloc(sizeof(double) * (size_t)M * (N / 2)));
+    if (!G || !partb || !s2b) {
+      cleanup();
+      return NS3D_ERR_OUT_OF_MEMORY;
+    }
+  }
   cplx<T>* twN = nullptr;
   double *mean = nullptr, *C = nullptr, *var = nullptr;
   T* phys = nullptr;
@@ -265,7 +375,7 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
     const size_t sms = 2 * sizeof(double) * (size_t)HL * nws;
     cudaFuncSetAttribute((const void*)k_spectra<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     k_spectra<T><<<N, 32 * nws, sms, s>>>(u, N, L.sp.kscale * L.sp.kscale, spec_t<double>(L.sp), part);
-    k_spectra_merge<<<cdiv(HL, 256), 256, 0, s>>>(part, N, HL, hist + (size_t)m * HL);
+    k_spectra_merge<<<cdiv(HL, 256), 256, 0, s>>>(part, N, HL, HL, hist + (size_t)m * HL);
     ok = cudaGetLastError() == cudaSuccess;
     if (!fields || !ok) continue;
     // inverse x and y without padding (n = N): column passes of the generic engine
@@ -288,6 +398,21 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
     k_zinv<T><<<dim3(cdiv(N, az.W), N), 128, smz, s>>>(az);
     k_welford<T><<<grid_of(N3), 256, 0, s>>>(phys, N3, m + 1, mean, C);
     ok = cudaGetLastError() == cudaSuccess;
+  }
+  std::vector<double> hb;
+  if (ball && ok) {
+    const BallCoef bc = ball_coefficients();
+    for (int j0 = 1; j0 <= N / 2 && ok; j0 += kBallJ) {
+      const int nj = std::min(kBallJ, N / 2 - j0 + 1);
+      k_ball_table<<<grid_of((long long)nj * nk2), 256, 0, s>>>(G, nk2, j0, nj, N, bc);
+      for (int m = 0; m < M; ++m) {
+        k_s2_ball<T><<<N, 256, 0, s>>>(U0 + m * g.nU, N, G, nk2, nj, partb);
+        k_spectra_merge<<<1, 32, 0, s>>>(partb, N, kBallJ, nj, s2b + (size_t)m * (N / 2) + j0 - 1);
+      }
+      ok = cudaGetLastError() == cudaSuccess;
+    }
+    hb.resize((size_t)M * (N / 2));
+    ok = ok && cudaMemcpyAsync(hb.data(), s2b, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s) == cudaSuccess;
   }
   std::vector<double> hh((size_t)HL * M);
   ok = ok && cudaMemcpyAsync(hh.data(), hist, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, s) == cudaSuccess;
@@ -344,6 +469,7 @@ ns3d_status stats_impl(ns3d_plan p, LevelView& L, ns3d_stats* out) {
   };
   mean_se(spec, N, out->spectrum, out->spectrum_se);
   mean_se(s2, N / 2, out->s2, out->s2_se);
+  if (ball) mean_se(hb, N / 2, out->s2_ball, out->s2_ball_se);
   mean_se(zspec, N, out->enstrophy_spectrum, out->enstrophy_spectrum_se);
   double emu = 0.0, ese = 0.0;
   mean_se(en, 1, &emu, &ese);

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-_PAIRS = ["spectrum", "s2", "energy", "enstrophy_spectrum", "enstrophy", "dissipation"]
+_PAIRS = ["spectrum", "s2", "s2_ball", "energy", "enstrophy_spectrum", "enstrophy", "dissipation"]
 
 
 def _m2_from_se(se, n):

@@ -22,11 +22,13 @@ def _as_api(st):
     return {"members": st["M"], "mean": st["mean"], "second": st["second"], "var": st["var"],
             "spectrum": st["spectrum"], "spectrum_se": st["spectrum_stderr"],
             "s2": st["s2"], "s2_se": st["s2_stderr"],
+            "s2_ball": st["s2_ball"], "s2_ball_se": st["s2_ball_stderr"],
             "energy": st["energy"], "energy_se": st["energy_stderr"]}
 
 
 def _close(a, b):
-    for k in ("mean", "second", "var", "spectrum", "spectrum_se", "s2", "s2_se", "energy", "energy_se"):
+    for k in ("mean", "second", "var", "spectrum", "spectrum_se", "s2", "s2_se", "s2_ball", "s2_ball_se",
+              "energy", "energy_se"):
         assert np.allclose(a[k], b[k], rtol=1e-11, atol=1e-14), k
     assert a["members"] == b["members"]
 

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 KEYS = [("mean", "mean"), ("second", "second"), ("var", "var"), ("spectrum", "spectrum"),
         ("spectrum_se", "spectrum_stderr"), ("s2", "s2"), ("s2_se", "s2_stderr"),
         ("enstrophy_spectrum", "enstrophy_spectrum"),
-        ("enstrophy_spectrum_se", "enstrophy_spectrum_stderr")]
+        ("enstrophy_spectrum_se", "enstrophy_spectrum_stderr"),
+        ("s2_ball", "s2_ball"), ("s2_ball_se", "s2_ball_stderr")]
 SCALARS = ["energy", "enstrophy", "dissipation"]
 
 
@@ -204,7 +205,7 @@ def test_spectra_are_compensated_and_reproducible(lib, N):
     p = B.Plan([N], B.NS3D_F64, eps0=1.0)
     p.set_initial(0, I.random_spectrum(N, seed=77, k0=0.3 * N))
     a, b = p.ensemble_stats(N), p.ensemble_stats(N)
-    for k in ("spectrum", "enstrophy_spectrum", "s2"):
+    for k in ("spectrum", "enstrophy_spectrum", "s2", "s2_ball"):
         assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
     for k in ("energy", "enstrophy", "dissipation"):
         assert a[k] == b[k], k
