@@ -25,6 +25,9 @@ int g_use_fast = 1;
 // nonlinear form of the emulated right-hand side (0 divergence, 1 advective,
 // 2 rotational)
 int g_form = 0;
+// > 0: the zform tile width W instead of the default shape (any shape the
+// plan's tuner may pick must compute the same values)
+int g_form_W = 0;
 
 // three-pass factorisations emulated at short lengths (the GPU builds them
 // for long lines only), so that their index logic meets the oracle
@@ -448,6 +451,15 @@ int run(int N, int P, const double* prm, const void* uin, void* uout, int nsteps
         double* t_out) {
   ns3d::Geom g;
   if (!ns3d::make_geom(N, P, (int)sizeof(cplx<T>), &g) || !ns3d::set_form_geom(&g, g_form)) return 1;
+  if (g_form_W > 0 && g.form != 0) {
+    bool found = false;
+    for (const ns3d::FormTile& t : ns3d::form_tile_candidates(g))
+      if (t.W == g_form_W && !found) {
+        ns3d::set_form_tile(&g, t);
+        found = true;
+      }
+    if (!found) return 1;
+  }
   // prm: L nu s theta eps0 mN_coef q_form cfl
   SpecParams sp = ns3d::make_spec_params(N, P, prm[0], prm[1], prm[2], prm[3], prm[4], prm[5],
                                          (int)prm[6], prm[7], dt);
@@ -509,6 +521,9 @@ void ns3d_hostcheck_use_fast(int mode) { g_use_fast = mode; }
 
 // nonlinear form of later ns3d_hostcheck_run calls (0, 1 or 2)
 void ns3d_hostcheck_set_form(int form) { g_form = form; }
+
+// zform tile width of later form-1/2 runs (0: the default shape)
+void ns3d_hostcheck_set_form_tile(int W) { g_form_W = W; }
 
 // One column pass of the three-pass kernel at P = 1536 (N = 1024) on a
 // [rows][ncols] array: sign > 0 the padded inverse (N rows in, P out),

@@ -152,6 +152,35 @@ inline bool set_form_geom(Geom* g, int form) {
   return true;
 }
 
+// Tile shapes the zform kernel can run at for this level: W y columns per
+// block (1 .. 16) and 128, 256 or 512 threads (FP32; FP64 kernels are built
+// for 128), within the shared memory of one block.  Every shape computes the
+// same values (each column's transforms do not depend on the tile); plan
+// creation times them and keeps the fastest.
+struct FormTile {
+  int W, nthr;
+  size_t smem;
+};
+
+inline std::vector<FormTile> form_tile_candidates(const Geom& g) {
+  std::vector<FormTile> c;
+  if (g.form == 0) return c;
+  const int nb = zform_buffers(g.form);
+  for (int W = 1; W <= 16; W *= 2)
+    for (int nthr = 128; nthr <= (g.esz == 8 ? 512 : 128); nthr *= 2) {
+      const size_t need = (size_t)nb * g.P * (W + 1) * g.esz + (size_t)8 * nthr;
+      if (need <= kSmemMax && W <= g.P) c.push_back({W, nthr, need});
+    }
+  return c;
+}
+
+inline void set_form_tile(Geom* g, const FormTile& t) {
+  g->Wzf = t.W;
+  g->ldwzf = t.W + 1;
+  g->nthr_zf = t.nthr;
+  g->smem_zf = t.smem;
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------- pass arguments

@@ -540,6 +540,78 @@ double time_rhs(int N, int P, ns3d_dtype dtype, ns3d_params prm, cudaStream_t s)
   return best;
 }
 
+// (device, N, P, dtype, form) -> index into form_tile_candidates
+std::map<std::tuple<std::string, int, int, int, int>, int> g_form_tile;
+
+// The zform tile of a form-1/2 level: each candidate shape timed on the first
+// x planes (at most 96) of member 0 in the level's own workspaces (zeroed
+// fields; one warm-up and two timed launches), the fastest kept and cached per
+// device.  The shape does not change the computed values.
+template <typename T>
+ns3d_status tune_form_tile(Level& L, ns3d_dtype dtype, cudaStream_t s) {
+  Geom& g = L.g;
+  const std::vector<FormTile> cand = form_tile_candidates(g);
+  if (cand.empty()) return NS3D_ERR_NOT_SUPPORTED;
+  int dev = 0;
+  cudaDeviceProp pr{};
+  std::string name = "unknown";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&pr, dev) == cudaSuccess)
+    name = pr.name;
+  const auto key = std::make_tuple(name, g.N, g.P, (int)dtype, g.form);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_form_tile.find(key);
+    if (it != g_form_tile.end()) {
+      set_form_tile(&g, cand[it->second]);
+      return NS3D_OK;
+    }
+  }
+  const long long P = g.P, h = g.h;
+  const int nf = form_fields(g.form);
+  NS3D_CK(cudaMemsetAsync(L.W1, 0, (size_t)nf * P * P * h * sizeof(cplx<T>), s));
+  ZArgs<T> az = args_z<T>(g, static_cast<const cplx<T>*>(L.W1), static_cast<cplx<T>*>(L.W2),
+                          static_cast<const cplx<T>*>(L.twP), nullptr);
+  az.in_bs = nf * P * P * h;
+  az.out_bs = 3 * P * P * h;
+  const int gy = (int)std::min<long long>(P, 96);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return NS3D_ERR_CUDA;
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    az.W = cand[c].W;
+    az.ldw = cand[c].W + 1;
+    const Launch lz{cdiv(P, cand[c].W), gy, 1, cand[c].nthr, cand[c].smem};
+    float ms = -1.f;
+    for (int r = 0; r < 3; ++r) {
+      float t = 0.f;
+      if (cudaEventRecord(e0, s) != cudaSuccess || launch_zform<T>(az, g.form, lz, s) != cudaSuccess ||
+          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+        cudaGetLastError();   // a shape the device cannot launch is skipped
+        ms = -1.f;
+        break;
+      }
+      if (r > 0 && (ms < 0 || t < ms)) ms = t;
+    }
+    if (ms >= 0 && (best < 0 || ms < best_ms)) {
+      best = (int)c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return NS3D_ERR_CUDA;
+  set_form_tile(&g, cand[best]);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_form_tile[key] = best;
+  return NS3D_OK;
+}
+
 int autotune_padded_size(int N, ns3d_dtype dtype, const ns3d_params& prm, cudaStream_t s) {
   const std::vector<int> cand = pad_candidates(N);
   if (cand.size() < 2 || register_kernels_at(N, cand[0], dtype)) return cand[0];
@@ -657,6 +729,11 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     L.ctrl = static_cast<Ns3dCtrl*>(c);
     st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
     if (st != NS3D_OK) break;
+    if (g.form != 0 && P.n_pad != -1) {
+      st = dtype == NS3D_F32 ? tune_form_tile<float>(L, dtype, p->stream)
+                             : tune_form_tile<double>(L, dtype, p->stream);
+      if (st != NS3D_OK) break;
+    }
     if (L.fused && !xfused_make_maps(&L.maps, g, L.B, L.W2, L.U0, L.US)) L.fused = false;
     if ((st = dev_alloc(p, &L.lamT, lambda_entries(g) * p->esz / 2)) != NS3D_OK) break;
     st = dtype == NS3D_F32 ? upload_lambda<float>(L, p->stream) : upload_lambda<double>(L, p->stream);

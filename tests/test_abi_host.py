@@ -165,6 +165,25 @@ def test_emulated_nonlinear_forms_match_oracle(built, form, N, P):
         lib.ns3d_hostcheck_set_form(0)
 
 
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("W", [1, 2, 8, 16])
+def test_emulated_form_tile_shapes(built, form, W):
+    """Every z tile width the plan's tuner may pick (ragged last tile at
+    P = 24 with W = 16, odd P = 35) gives the oracle's RHS."""
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_set_form(form)
+    lib.ns3d_hostcheck_set_form_tile(W)
+    try:
+        prm = S.Params(nu=0.01, eps0=1.0, nonlinear_form=form)
+        for N, P in ((16, 24), (22, 35)):
+            uh = I.random_spectrum(N, seed=5 * W + form, k0=2.5)
+            got, rc, _ = hostcheck(built, uh, P, prm)
+            assert rc == 0 and rel(got, S.rhs(uh, prm, P=P)) < 1e-13, (N, P)
+    finally:
+        lib.ns3d_hostcheck_set_form_tile(0)
+        lib.ns3d_hostcheck_set_form(0)
+
+
 def test_radix_plans(built):
     lib = ctypes.CDLL(built.HOSTLIB)
     r = (ctypes.c_int * 8)()
