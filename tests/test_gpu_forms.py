@@ -109,3 +109,20 @@ def test_form_nonfinite_sets_status(B, form):
         p.synchronize()
     assert e.value.code == 4
     p.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_form_plan_gradient(B, form):
+    """The band-energy gradient of a form-1/2 plan (forward stages recomputed
+    in that form, the transpose of the divergence form's linearisation) equals
+    the divergence form's gradient and the oracle's, up to rounding."""
+    from oracle import adjoint as A
+    N, dt, n = 12, 0.04, 6
+    prm = S.Params(nu=0.01, eps0=1.0)
+    u0 = I.random_spectrum(N, seed=8, k0=2.5)
+    p = B.Plan([N], B.NS3D_F64, nu=0.01, eps0=1.0, dt_fixed=dt, nonlinear_form=form)
+    p.set_initial(0, u0)
+    got = p.grad_band_energy(0, 2.0, 4.0, n, checkpoint_every=4).cpu().numpy()
+    p.close()
+    ref = A.grad_band_energy(u0, prm, n, dt, 2.0, 4.0, checkpoint_every=4)
+    assert rel(got, ref) < 1e-11
