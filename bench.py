@@ -100,6 +100,22 @@ def bench_ensemble(B, torch, steps: int, warmup: int, to_t: float = 0.0):
     return info
 
 
+# FP64 arithmetic peak of one GB300 from its unit counts: 152 SMs x 2 FP64 FMA
+# (4 flops) per SM per clock x the 2070 MHz maximum SM clock = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+def fft_flops_per_step(N: int, P: int) -> float:
+    """Algorithmic flops of one RK3 step: 5 P log2 P per complex line of
+    length P over the line families of one right-hand side (inverse x 3 N h,
+    inverse y 3 P h, z 4.5 P^2 = 1.5 inverse + 3 forward packed complex lines,
+    forward y 6 P h, forward x 6 N h; h = N/2), three evaluations per step."""
+    import math
+    h = N // 2
+    lines = 3 * N * h + 3 * P * h + 4.5 * P * P + 6 * P * h + 6 * N * h
+    return 3.0 * lines * 5.0 * P * math.log2(P)
+
+
 def bench_plain_fp64(B, torch, N: int, steps: int):
     """The plain FP64 path on the main workload, and the FP32 path's relative
     L2 error against it: one right-hand side, and the state after 10 steps."""
@@ -129,9 +145,15 @@ def bench_plain_fp64(B, torch, N: int, steps: int):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    P = plan.info(0)["P"]
     plan.close()
+    ach = fft_flops_per_step(N, P) / (ms / steps * 1e-3) / 1e12
     return {"N": N, "steps": steps, "ms_per_step": ms / steps,
-            "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT, "f32_error_vs_f64": err}
+            "value": N ** 3 * steps / (ms * 1e-3), "unit": UNIT, "f32_error_vs_f64": err,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "peak_kind": "unit counts x max clock", "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS,
+                         "flops_per_step": fft_flops_per_step(N, P)}}
 
 
 def bench_forms(B, torch, N: int, steps: int = 5):
@@ -216,6 +238,10 @@ def bench_largest(B, torch, cases=((1024, "f32", 4), (768, "f64", 2))):
                         "kernel_ms": {k: kms[i] / max(kn[i], 1) for i, k in enumerate(KINDS) if kn[i]},
                         "bytes_per_step_GB": step_bytes / 1e9,
                         "achieved_GBps": step_bytes / (ms * 1e-3) / 1e9})
+            if dt == "f64":   # the FP64 path is bound by the FP64 units, not by HBM
+                ach = fft_flops_per_step(N, P) / (ms * 1e-3) / 1e12
+                rec["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                                   "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS}
         except Exception as e:   # recorded, not fatal: the main line still prints
             rec["error"] = str(e).splitlines()[0][:200]
         finally:
