@@ -15,6 +15,7 @@
 #include "ns3d_xfused.cuh"
 #include "ns3d_colfast3.cuh"
 #include "ns3d_zfast3.cuh"
+#include "ns3d_zrot.cuh"
 
 namespace {
 
@@ -134,6 +135,32 @@ void run_z(const ZArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   for (int z = 0; z < L.gz; ++z)
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < L.gx; ++x) zfused_block<T>(a, x, y, z, 0, 1, sm.data(), red, HostSync{});
+}
+
+// The rotational form's register-resident z pass, phase by phase and thread
+// by thread.
+template <typename T, int N1, int N2>
+void run_zrot(const ZArgs<T>& a, int nm) {
+  using S = ZRotShape<N1, N2>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<T> red(S::NTHR);
+  std::vector<ZFastState<T, N1, N2>> st(S::NTHR);
+  const int gx = (S::P + S::Y - 1) / S::Y;
+  for (int bz = 0; bz < nm; ++bz)
+    for (int by = 0; by < S::P; ++by)
+      for (int bx = 0; bx < gx; ++bx) {
+        ZFastCtx<T, N1, N2> c = zrot_ctx<T, N1, N2>(a, bx, by, bz, sm.data());
+        for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zrot_inv1(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) {
+          zrot_inv2(c, t, st[t]);
+          red[t] = st[t].bad ? T(-1) : st[t].umax;
+        }
+        zfast_reduce(c, red.data(), S::NTHR, 0);
+        for (int t = 0; t < S::NTHR; ++t) zrot_fwd1(c, t, st[t]);
+        for (int t = 0; t < S::NTHR; ++t) zrot_fwd2(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zrot_extract(c, t, S::NTHR);
+      }
 }
 
 template <typename T>
@@ -383,7 +410,17 @@ void rhs_stage_form(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in
   az.ldw = g.ldwzf;
   az.in_bs = nf * P * P * h;
   az.out_bs = 3 * P * P * h;
-  run_zform<T>(az, g.form, Launch{cdiv(P, g.Wzf), g.P, 1, g.nthr_zf, g.smem_zf}, sm);
+  bool done = false;
+  if (g_use_fast && g_form_W == 0 && sizeof(T) == 4 && g.form == 2 && 3 * g.h == g.P) {
+#define NS3D_HC_ZR(A, B)            \
+    if (g.P == (A) * (B)) {         \
+      run_zrot<T, A, B>(az, 1);     \
+      done = true;                  \
+    }
+    NS3D_FOR_ZFAST(NS3D_HC_ZR)
+#undef NS3D_HC_ZR
+  }
+  if (!done) run_zform<T>(az, g.form, Launch{cdiv(P, g.Wzf), g.P, 1, g.nthr_zf, g.smem_zf}, sm);
   Launch lfy = launch_fwd_y(g, 1);
   lfy.gz = 3;
   run_col<T, -1, true, true>(args_fwd_y<T>(g, W2.data(), W1.data(), tw.data()), lfy, sm);

@@ -3,6 +3,7 @@
 
 #include "kernels_col.cuh"
 #include "ns3d_zfast.cuh"
+#include "ns3d_zrot.cuh"
 
 namespace ns3d {
 
@@ -55,10 +56,57 @@ cudaError_t zfast_init() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
+// The rotational form's register-resident z pass (ns3d_zrot.cuh), same sizes.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(ZRotShape<N1, N2>::NTHR, 384 / ZRotShape<N1, N2>::NTHR) k_zrot(ZArgs<T> a) {
+  using S = ZRotShape<N1, N2>;
+  extern __shared__ __align__(16) unsigned char ns3d_smem[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  T* red = reinterpret_cast<T*>(sm + S::SM_ELEMS);
+  const ZFastCtx<T, N1, N2> c = zrot_ctx<T, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+  const int tid = threadIdx.x;
+  zfast_load_twiddles(c, tid, S::NTHR);
+  __syncthreads();
+  zrot_inv1(c, tid, S::NTHR);
+  __syncthreads();
+  ZFastState<T, N1, N2> st;
+  zrot_inv2(c, tid, st);
+  red[tid] = st.bad ? T(-1) : st.umax;
+  __syncthreads();
+  if (tid < 32) zfast_reduce(c, red, S::NTHR, tid);
+  zrot_fwd1(c, tid, st);
+  __syncthreads();
+  zrot_fwd2(c, tid, S::NTHR);
+  __syncthreads();
+  zrot_extract(c, tid, S::NTHR);
+}
+
+template <typename T, int N1, int N2>
+size_t zrot_smem() {
+  using S = ZRotShape<N1, N2>;
+  return (size_t)S::SM_ELEMS * sizeof(cplx<T>) + (size_t)S::NTHR * sizeof(double);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zrot_launch(const ZArgs<T>& a, int nm, cudaStream_t s) {
+  using S = ZRotShape<N1, N2>;
+  dim3 grid((S::P + S::Y - 1) / S::Y, S::P, nm);
+  k_zrot<T, N1, N2><<<grid, S::NTHR, zrot_smem<T, N1, N2>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zrot_init() {
+  return cudaFuncSetAttribute((const void*)k_zrot<T, N1, N2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 }  // namespace ns3d
 
 #define NS3D_ZFAST_VARIANT(T, N1, N2)                                                        \
   namespace ns3d {                                                                           \
   template cudaError_t zfast_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);          \
   template cudaError_t zfast_init<T, N1, N2>();                                              \
+  template cudaError_t zrot_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);           \
+  template cudaError_t zrot_init<T, N1, N2>();                                               \
   }

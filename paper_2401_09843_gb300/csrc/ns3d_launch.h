@@ -140,6 +140,10 @@ template <typename T, int N1, int N2>
 cudaError_t zfast_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
 template <typename T, int N1, int N2>
 cudaError_t zfast_init();
+template <typename T, int N1, int N2>
+cudaError_t zrot_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t zrot_init();
 
 
 template <typename T>
@@ -165,6 +169,13 @@ bool zfast_available(int P) {
   return false;
 }
 
+// the rotational form's register-resident z pass exists for this level
+inline bool zrot_available(const Geom& g) {
+  return g.form == 2 && g.esz == 8 && 3 * g.h == g.P && zfast_available<float>(g.P);
+}
+
+
+
 // The fused z pass of a level: the register-resident kernel where one exists
 // for (T, P), the generic tile kernel otherwise.
 template <typename T>
@@ -181,6 +192,20 @@ template <typename T>
 cudaError_t launch_zform(const ZArgs<T>& a, int form, const Launch& L, cudaStream_t s);
 template <typename T>
 cudaError_t zform_init();
+
+// z pass of a form-1/2 level: the rotational register kernel where it exists,
+// else the tuned zform tile kernel
+template <typename T>
+cudaError_t launch_zform_level(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t s) {
+  if (sizeof(T) == 4 && zrot_available(g)) {
+    const ZArgs<float>& af = *reinterpret_cast<const ZArgs<float>*>(&a);
+#define NS3D_ZR_GO(A, B) \
+    if (g.P == (A) * (B)) return zrot_launch<float, A, B>(af, nm, s);
+    NS3D_FOR_ZFAST(NS3D_ZR_GO)
+#undef NS3D_ZR_GO
+  }
+  return launch_zform<T>(a, g.form, Launch{cdiv(g.P, g.Wzf), g.P, nm, g.nthr_zf, g.smem_zf}, s);
+}
 // per-member time step of the step starting now (before the stage-1 spectral kernel)
 cudaError_t launch_step_dt(Ns3dCtrl* c, int n, const SpecParams& sp, cudaStream_t s);
 template <typename T>
@@ -214,6 +239,7 @@ cudaError_t kernels_init() {
 #define NS3D_ZF_INIT(A, B)                                  \
     {                                                       \
       cudaError_t r = zfast_init<float, A, B>();            \
+      if (r == cudaSuccess) r = zrot_init<float, A, B>();   \
       if (r != cudaSuccess) return r;                       \
     }
     NS3D_FOR_ZFAST(NS3D_ZF_INIT)

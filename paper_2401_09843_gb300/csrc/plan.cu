@@ -271,7 +271,7 @@ ns3d_status enqueue_rhs_form(const StageBufs& b, int stage, int nm, const cplx<T
   az.ldw = g.ldwzf;
   az.in_bs = nf * P * P * h;
   az.out_bs = 3 * P * P * h;
-  NS3D_CK(launch_zform<T>(az, g.form, Launch{cdiv(P, g.Wzf), g.P, nm, g.nthr_zf, g.smem_zf}, s));
+  NS3D_CK(launch_zform_level<T>(az, g, nm, s));
   NS3D_MARK(3);
   Launch lfy = launch_fwd_y(g, nm);
   lfy.gz = nm * 3;
@@ -729,7 +729,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     L.ctrl = static_cast<Ns3dCtrl*>(c);
     st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
     if (st != NS3D_OK) break;
-    if (g.form != 0 && P.n_pad != -1) {
+    if (g.form != 0 && P.n_pad != -1 && !zrot_available(g)) {
       st = dtype == NS3D_F32 ? tune_form_tile<float>(L, dtype, p->stream)
                              : tune_form_tile<double>(L, dtype, p->stream);
       if (st != NS3D_OK) break;

@@ -213,6 +213,30 @@ def test_emulated_register_kernels_match_oracle(built, N, P):
     assert rel(gen32, ref) < 2e-6
 
 
+@pytest.mark.parametrize("N,P", [(32, 48), (64, 96), (128, 192), (256, 384)])
+def test_emulated_rotational_register_z_pass(built, N, P):
+    """The rotational form's register-resident z pass (FP32, P = 3N/2),
+    emulated thread by thread, against the Galerkin product of a sparse field
+    (equal for every form after the projection); then the tile kernel."""
+    prm = S.Params(nu=0.01, eps0=1.0, nonlinear_form=2)
+    uh = I.sparse_random(N, seed=P + 1, nmodes=24)
+    ref = S.rhs_by_convolution(uh, prm)
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_set_form(2)
+    try:
+        got32, rc, _ = hostcheck(built, uh, P, prm, dtype=0)
+        assert rc == 0 and rel(got32, ref) < 2e-6
+        if N <= 64:
+            lib.ns3d_hostcheck_use_fast(0)
+            try:
+                gen32, _, _ = hostcheck(built, uh, P, prm, dtype=0)
+            finally:
+                lib.ns3d_hostcheck_use_fast(1)
+            assert rel(gen32, ref) < 2e-6
+    finally:
+        lib.ns3d_hostcheck_set_form(0)
+
+
 @pytest.mark.parametrize("N", [32, 64])
 def test_emulated_fused_x_steps_match_oracle(built, N):
     """Steps with the fused x pass (forward x + spectral + RK3 + next inverse x
