@@ -82,9 +82,12 @@ typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
  *          derivatives: 12 inverse and 3 forward.  2 = rotational form
  *          F[u x curl u]: 6 inverse and 3 forward.  For a divergence-free
  *          field with 3/2 padding the three agree after the projection up to
- *          rounding.  Forms 1 and 2 run the generic tile kernels, take the
- *          smallest 7-smooth padded size when n_pad = 0 (no benchmark), and
- *          need more workspace (form 1: twice that of form 0).
+ *          rounding.  Forms 1 and 2 take the smallest 7-smooth padded size
+ *          when n_pad = 0 (no benchmark) and need more workspace (form 1:
+ *          twice that of form 0); their z pass is a register-resident kernel
+ *          for form 2 in FP32 at P = 3N/2 in {48, 96, 192, 384}, otherwise a
+ *          tile kernel whose tile shape plan creation times and picks
+ *          (n_pad = -1 keeps a fixed shape).
  *          ns3d_eval_rhs_noalloc takes form 0 only.
  *   dt_fixed > 0: fixed time step; otherwise dt = cfl * (L/N) / max_x sum_i |u_i|
  *          evaluated on the padded grid of the stage-1 field, per member. */
