@@ -117,6 +117,25 @@ def test_beltrami_and_2d_tg_nonlinear_term_projects_out(field):
         assert np.max(np.abs(pb)) < 1e-14 * max(1.0, np.max(np.abs(b))), form
 
 
+def test_2d_taylor_green_nonlinear_term_closed_forms():
+    """b before the projection, each form against its own closed form for
+    u = (sin x cos y, -cos x sin y, 0): (u.grad)u = 1/2 (sin 2x, sin 2y, 0) (and
+    div(u u) is the same, u being divergence-free), so forms 0 and 1 give
+    b = -1/2 (sin 2x, sin 2y, 0); with omega = (0, 0, 2 sin x sin y),
+    u x omega = (-sin 2x sin^2 y, -sin^2 x sin 2y, 0) for form 2.  A transposed
+    gradient (grad |u|^2/2 instead) or a swapped cross product fails."""
+    N = 16
+    uh = I.taylor_green_2d(N)
+    adv = I.coefficients_of(sample(lambda X, Y, Z: -0.5 * np.stack([
+        np.sin(2 * X), np.sin(2 * Y), 0.0 * Z]), N))
+    rot = I.coefficients_of(sample(lambda X, Y, Z: np.stack([
+        -np.sin(2 * X) * np.sin(Y) ** 2, -np.sin(X) ** 2 * np.sin(2 * Y), 0.0 * Z]), N))
+    for form, expect in ((0, adv), (1, adv), (2, rot)):
+        b, umax = S.nonlinear(uh, EULER, form=form)
+        assert np.max(np.abs(b - expect)) < 1e-15, form
+        assert abs(umax - 1.0) < 1e-15     # max |sin x cos y| + |cos x sin y| = 1 at x = y = pi/4
+
+
 def test_three_nonlinear_forms_agree():
     N = 16
     uh = I.random_spectrum(N, seed=5, k0=3.0)
