@@ -126,3 +126,21 @@ def test_form_plan_gradient(B, form):
     p.close()
     ref = A.grad_band_energy(u0, prm, n, dt, 2.0, 4.0, checkpoint_every=4)
     assert rel(got, ref) < 1e-11
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_form_rhs_full_size_sparse_spectrum(B, form, dt):
+    """256^3 in the production launch shapes (FP32 rotational form: the
+    register-resident z pass; otherwise the tuned tile kernel) against the
+    truncated product of a divergence-free sparse field summed over mode
+    pairs, which every form equals after the projection."""
+    N = 256
+    dtype = B.NS3D_F64 if dt == "f64" else B.NS3D_F32
+    prm = S.Params(nu=0.0, eps0=1.0)
+    uh = I.sparse_random(N, seed=N + 7 + form, nmodes=48)
+    ref = S.rhs_by_convolution(uh, prm)
+    p = B.Plan([N], dtype, nu=0.0, eps0=1.0, nonlinear_form=form)
+    got = p.eval_rhs(0, uh).cpu().numpy()
+    p.close()
+    assert rel(got, ref) < (TOL64 if dt == "f64" else TOL32)
