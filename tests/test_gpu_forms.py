@@ -144,3 +144,23 @@ def test_form_rhs_full_size_sparse_spectrum(B, form, dt):
     got = p.eval_rhs(0, uh).cpu().numpy()
     p.close()
     assert rel(got, ref) < (TOL64 if dt == "f64" else TOL32)
+
+
+def test_rotational_register_kernel_two_members(B):
+    """Two members in one level at a register size (FP32, P = 48): each
+    member's RHS and CFL steps (per-member dt from the kernel's CFL maximum)
+    against the oracle."""
+    N = 32
+    prm = S.Params(cfl=0.5, eps0=1.0, nonlinear_form=2)
+    u0 = [I.random_spectrum(N, seed=70 + m, k0=2.0 + m) for m in range(2)]
+    p = B.Plan([N, N], B.NS3D_F32, cfl=0.5, eps0=1.0, nonlinear_form=2)
+    for m in range(2):
+        assert rel(p.eval_rhs(m, u0[m]).cpu().numpy(), S.rhs(u0[m], prm, P=48)) < TOL32, m
+        p.set_initial(m, u0[m])
+    p.step(3)
+    for m in range(2):
+        got, t = p.get_state(m, with_time=True)
+        ref, tref, _ = S.integrate(u0[m], prm, 3, P=48)
+        assert abs(t - tref) < 1e-6 * tref, m
+        assert rel(got.cpu().numpy(), ref) < TOL32, m
+    p.close()
