@@ -42,6 +42,22 @@ from . import fft as _fft
 
 TWO_PI = 2.0 * math.pi
 
+# The per-component transforms of one right-hand side are independent; they
+# run through _MAP, the builtin map unless ``set_map`` installs a process
+# pool's map.  Each component's arithmetic is the same either way, so the
+# results are bitwise identical.
+_MAP = map
+
+
+def set_map(fn=None):
+    """Install ``fn`` (e.g. a spawn-started process pool's ``map``) for the
+    independent per-component transforms of ``nonlinear``; None restores the
+    builtin map.  Returns the previous one."""
+    global _MAP
+    old = _MAP
+    _MAP = map if fn is None else fn
+    return old
+
 
 @dataclass(frozen=True)
 class Params:
@@ -226,6 +242,16 @@ def to_spectral(b: np.ndarray, N: int) -> np.ndarray:
     return out * retained_mask(N)
 
 
+def _to_physical_task(args):
+    uh, P = args
+    return to_physical(uh, P)
+
+
+def _to_spectral_task(args):
+    b, N = args
+    return to_spectral(b, N)
+
+
 # ---------------------------------------------------------------- right-hand side
 
 def leray(b: np.ndarray, L: float) -> np.ndarray:
@@ -250,14 +276,14 @@ def nonlinear(uhat: np.ndarray, prm: Params, P: int | None = None, form: int | N
     P = P or padded_size(N, prm.n_pad)
     form = prm.nonlinear_form if form is None else form
     k = kappa(N, prm.L)
-    u = to_physical(uhat, P)
+    u = np.stack(list(_MAP(_to_physical_task, [(uhat[c], P) for c in range(3)])))
     umax = float(np.max(np.abs(u[0]) + np.abs(u[1]) + np.abs(u[2])))
     if form == 0:
+        pairs = [(j, l) for j in range(3) for l in range(j, 3)]
         Bhat = {}
-        for j in range(3):
-            for l in range(j, 3):
-                Bhat[j, l] = to_spectral(u[j] * u[l], N)
-                Bhat[l, j] = Bhat[j, l]
+        for (j, l), v in zip(pairs, _MAP(_to_spectral_task, [(u[j] * u[l], N) for j, l in pairs])):
+            Bhat[j, l] = v
+            Bhat[l, j] = v
         b = np.stack([-1j * sum(k[l] * Bhat[j, l] for l in range(3)) for j in range(3)])
     elif form == 1:
         a = np.zeros_like(u)
@@ -294,25 +320,33 @@ def cfl_dt(umax: float, N: int, prm: Params) -> float:
 
 
 def rk3_step(uhat: np.ndarray, prm: Params, dt: float | None = None, P: int | None = None,
-             t: float = 0.0, t_end: float = 0.0):
+             t: float = 0.0, t_end: float = 0.0, rhs_fn=None):
     """One SSP-RK3 step (eq. RK3):
         u1 = u + dt R(u)
         u2 = 3/4 u + 1/4 u1 + 1/4 dt R(u1)
         u+ = 1/3 u + 2/3 u2 + 2/3 dt R(u2)
     dt: given, else prm.dt_fixed if > 0, else the CFL step of the stage-1
     field; clipped so that t + dt <= t_end when t_end > 0 (a member that has
-    reached t_end does not move).  Returns (u+, dt)."""
+    reached t_end does not move).  rhs_fn: another evaluation of R (e.g.
+    ``rhs_by_convolution`` for sparse spectra on large grids); it gives no
+    CFL maximum, so dt or prm.dt_fixed must then be set.  Returns (u+, dt)."""
     N = uhat.shape[-2]
-    R0, umax = rhs(uhat, prm, P, return_umax=True)
+    if rhs_fn is None:
+        R0, umax = rhs(uhat, prm, P, return_umax=True)
+    else:
+        R0, umax = rhs_fn(uhat), None
+        if dt is None and not prm.dt_fixed > 0:
+            raise ValueError("rhs_fn needs a given dt or prm.dt_fixed")
     if dt is None:
         dt = prm.dt_fixed if prm.dt_fixed > 0 else cfl_dt(umax, N, prm)
         if t_end > 0:
             dt = min(dt, t_end - t)
             if dt <= 0:
                 return uhat.copy(), 0.0
+    f = (lambda v: rhs(v, prm, P)) if rhs_fn is None else rhs_fn
     u1 = uhat + dt * R0
-    u2 = 0.75 * uhat + 0.25 * u1 + 0.25 * dt * rhs(u1, prm, P)
-    un = uhat / 3.0 + (2.0 / 3.0) * u2 + (2.0 / 3.0) * dt * rhs(u2, prm, P)
+    u2 = 0.75 * uhat + 0.25 * u1 + 0.25 * dt * f(u1)
+    un = uhat / 3.0 + (2.0 / 3.0) * u2 + (2.0 / 3.0) * dt * f(u2)
     return un, dt
 
 
@@ -337,11 +371,13 @@ def rk3_amplification(z: complex) -> complex:
 
 # ---------------------------------------------------------------- sparse fields
 
-def nonlinear_by_convolution(uhat: np.ndarray, prm: Params) -> np.ndarray:
+def nonlinear_by_convolution(uhat: np.ndarray, prm: Params, chunk_pairs: int = 1 << 22) -> np.ndarray:
     """b_hat of the divergence form from the Galerkin definition of the
     truncated product, B_hat_k = sum_{p + q = k} u_hat_p (x) u_hat_q over the
     full spectrum, for k in K_N.  Cost grows with the square of the number of
-    nonzero modes: meant for sparse spectra at any N (no transform, no grid)."""
+    nonzero modes: meant for sparse spectra at any N (no transform, no grid).
+    The pairs (p, q) are visited row by row in blocks of about
+    ``chunk_pairs``; every sum still adds its terms in the same order."""
     N = uhat.shape[-2]
     h = N // 2
     kx, ky, kz = wavenumbers(N)
@@ -353,16 +389,20 @@ def nonlinear_by_convolution(uhat: np.ndarray, prm: Params) -> np.ndarray:
     pos = K[:, 2] > 0                                  # mirror kz > 0 to -k
     K = np.concatenate([K, -K[pos]])
     V = np.concatenate([V, np.conj(V[pos])])
-    ksum = K[:, None, :] + K[None, :, :]               # (n, n, 3)
-    keep = (np.abs(ksum[..., 0]) < h) & (np.abs(ksum[..., 1]) < h) & (ksum[..., 2] >= 0) & (ksum[..., 2] < h)
-    ii, jj = np.nonzero(keep)
-    ks = ksum[ii, jj]
-    a = 2 * np.pi / prm.L
+    n = len(K)
     B = np.zeros((3, 3) + shape, dtype=np.complex128)
-    ix, iy, iz = ks[:, 0] % N, ks[:, 1] % N, ks[:, 2]
-    for j in range(3):
-        for l in range(3):
-            np.add.at(B[j, l], (ix, iy, iz), V[ii, j] * V[jj, l])
+    rows = max(1, chunk_pairs // max(n, 1))
+    for i0 in range(0, n, rows):
+        ksum = K[i0:i0 + rows, None, :] + K[None, :, :]      # (rows, n, 3)
+        keep = (np.abs(ksum[..., 0]) < h) & (np.abs(ksum[..., 1]) < h) & \
+               (ksum[..., 2] >= 0) & (ksum[..., 2] < h)
+        ii, jj = np.nonzero(keep)
+        ks = ksum[ii, jj]
+        ii = ii + i0
+        ix, iy, iz = ks[:, 0] % N, ks[:, 1] % N, ks[:, 2]
+        for j in range(3):
+            for l in range(3):
+                np.add.at(B[j, l], (ix, iy, iz), V[ii, j] * V[jj, l])
     kap = kappa(N, prm.L)
     b = np.stack([-1j * sum(kap[l] * B[j, l] for l in range(3)) for j in range(3)])
     return b * retained_mask(N)

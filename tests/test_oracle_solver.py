@@ -314,3 +314,60 @@ def test_rhs_sparse_matches_transform_rhs(N):
     assert np.linalg.norm(got - ref) < 1e-14 * np.linalg.norm(ref)
     K2, V2 = I.modes_of(u)
     assert np.array_equal(np.sort(K2, axis=0), np.sort(K, axis=0))
+
+
+@pytest.mark.parametrize("N", [12, 16, 24])
+def test_rhs_by_convolution_matches_transform_rhs(N):
+    """The Galerkin product summed over mode pairs of a dense D1 array (the
+    sparse-spectrum check used on full-size grids) equals the padded-transform
+    RHS; visiting the pairs in small row blocks changes no bit."""
+    u = I.sparse_random(N, seed=3 * N, nmodes=12)
+    prm = S.Params(nu=0.01, eps0=1.0)
+    ref = S.rhs(u, prm)
+    got = S.rhs_by_convolution(u, prm)
+    assert np.linalg.norm(got - ref) < 1e-14 * np.linalg.norm(ref)
+    b_one = S.nonlinear_by_convolution(u, prm)
+    b_rows = S.nonlinear_by_convolution(u, prm, chunk_pairs=7)
+    assert np.array_equal(b_one, b_rows)
+
+
+@pytest.mark.parametrize("N", [16, 24])
+def test_rk3_step_with_convolution_rhs_matches_transform_step(N):
+    """One SSP-RK3 step composed from the mode-pair Galerkin sum (three stages,
+    the support growing by pair sums at each) equals the padded-transform
+    step; the increment u+ - u agrees too, so a wrong stage weight shows."""
+    u = I.sparse_random(N, seed=5 * N, nmodes=4)
+    prm = S.Params(nu=0.0, eps0=1.0, dt_fixed=0.01)
+    ref, dt = S.rk3_step(u, prm)
+    got, dt2 = S.rk3_step(u, prm, rhs_fn=lambda v: S.rhs_by_convolution(v, prm))
+    assert dt == dt2 == 0.01
+    assert np.linalg.norm(got - ref) < 1e-14 * np.linalg.norm(ref)
+    assert np.linalg.norm((got - u) - (ref - u)) < 1e-13 * np.linalg.norm(ref - u)
+    # the step reached modes far outside the initial support
+    assert np.count_nonzero(np.any(ref != 0, axis=0)) > 20 * np.count_nonzero(np.any(u != 0, axis=0))
+    with pytest.raises(ValueError):
+        S.rk3_step(u, prm.with_(dt_fixed=0.0), rhs_fn=lambda v: S.rhs_by_convolution(v, prm))
+
+
+def _square(x):
+    return x * x
+
+
+def test_process_pool_map_gives_identical_rhs():
+    """The per-component transforms of one RHS run through a spawn-started
+    process pool when one is installed: the result is bitwise that of the
+    serial map."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    N = 16
+    u = I.random_spectrum(N, seed=77)
+    prm = S.Params(nu=0.01, eps0=1.0)
+    serial = S.rhs(u, prm)
+    with cf.ProcessPoolExecutor(2, mp_context=mp.get_context("spawn")) as ex:
+        old = S.set_map(ex.map)
+        try:
+            par = S.rhs(u, prm)
+        finally:
+            S.set_map(old)
+    assert np.array_equal(par, serial)
+    assert S.set_map(None) is map
