@@ -189,6 +189,16 @@ ns3d_status ns3d_grad_band_energy(ns3d_plan plan, int member, double k_lo, doubl
                                   int nsteps, int checkpoint_every, void* grad_uhat0,
                                   int on_device);
 
+/* The observable of ns3d_grad_band_energy at member `member`'s current state:
+ * J = 1/2 sum_{k_lo <= |k| < k_hi} |u_hat_k|^2 over the full spectrum (the
+ * energy of a band of shells, here the end-time observable whose gradient the
+ * discrete adjoint gives; not in the paper, which defines the energy
+ * spectrum of section 2.4).  Summed in FP64 with compensation in a fixed
+ * order (reproducible bit for bit) and written to the host double *J.
+ * Synchronises; returns the member's sticky device status like
+ * ns3d_get_state.  Errors: INVALID_ARG (null, k_hi <= k_lo, bad member). */
+ns3d_status ns3d_band_energy(ns3d_plan plan, int member, double k_lo, double k_hi, double* J);
+
 /* Ensemble statistics of the members of resolution level_N at their current
  * state (writers of section 2.4; Algorithm 1 step 3), accumulated in FP64 on
  * the device.  Every array is host memory owned by the caller; any pointer may
@@ -271,18 +281,24 @@ ns3d_status ns3d_step_timed(ns3d_plan plan, int nsteps, double t_end, double* ke
 
 /* Allocation-free right-hand side for small grids (the paper has no
  * counterpart; it is a service for callers that may not allocate device
- * memory when they need the derivative, e.g. code running inside another
- * component's CUDA graph capture or hosts with a memory budget fixed at start-up).
- * Computes the same R(u_hat) as ns3d_eval_rhs without a plan: uhat and
- * rhs_out are device buffers of the current device in D1 layout and `dtype`,
- * all work is enqueued on cuda_stream (a cudaStream_t) and nothing waits.
- * Every intermediate array lives in one 8 MiB file-scope device array of the
- * library (held by every GPU that loads it until exit); no cudaMalloc or other
- * allocation happens.  Limits: 4 <= N <= 32 and padded size P <= 48, else
- * NS3D_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and should come before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race;
- * order them on one stream. */
+ * memory when they need the derivative: hosts whose device memory budget is
+ * fixed at start-up, plug-ins that must not re-enter the host's allocator
+ * from a callback, loops that cannot afford cudaMalloc's implicit device
+ * synchronisation).  Computes the same R(u_hat) as ns3d_eval_rhs without a
+ * plan: uhat and rhs_out are device buffers of the current device in D1
+ * layout and `dtype`, all work is enqueued on cuda_stream (a cudaStream_t)
+ * and nothing waits.  Every intermediate array lives in one 8 MiB file-scope
+ * device array of the library (held by every GPU that loads it until exit);
+ * no cudaMalloc or other allocation happens.  Limits: 4 <= N <= 32 and padded
+ * size P <= 48, else NS3D_ERR_INVALID_ARG; n_pad 0 or -1 takes the smallest
+ * 7-smooth P >= 3N/2, and a given P with a prime factor above 7 returns
+ * NS3D_ERR_NOT_SUPPORTED (as ns3d_plan_create does).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process, so that call should come before any
+ * stream capture, and after a cudaDeviceReset of that device this entry point
+ * must not be called again.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU race; order them on one
+ * stream. */
 ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d_params* p,
                                   const void* uhat, void* rhs_out, void* cuda_stream);
 

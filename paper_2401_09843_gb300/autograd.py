@@ -2,8 +2,10 @@
 
 ``band_energy(uhat0, k_lo, k_hi, nsteps, ...)`` advances u_hat(0) by nsteps
 fixed SSP-RK3 steps on the GPU and returns J = 1/2 sum_{k_lo <= |k| < k_hi}
-|u_hat_k(T)|^2 over the full spectrum; its backward pass calls
-ns3d_grad_band_energy (the exact discrete adjoint, checkpoint/recompute).
+|u_hat_k(T)|^2 over the full spectrum, evaluated by ns3d_band_energy; its
+backward pass calls ns3d_grad_band_energy (the exact discrete adjoint,
+checkpoint/recompute).  This module only marshals arguments: no step of the
+observable or its gradient is computed here.
 
 Gradient convention: for the D1 tensor of stored coefficients, PyTorch's
 gradient of a real J is dJ/dRe z + i dJ/dIm z; the full-spectrum gradient g
@@ -24,29 +26,15 @@ def _weights(N: int, device):
     return w
 
 
-def _band(N: int, k_lo: float, k_hi: float, device):
-    k = torch.fft.fftfreq(N, 1.0 / N, device=device, dtype=torch.float64)
-    kz = torch.arange(N // 2 + 1, device=device, dtype=torch.float64)
-    km = torch.sqrt(k[:, None, None] ** 2 + k[None, :, None] ** 2 + kz[None, None, :] ** 2)
-    h = N // 2
-    keep = (km >= k_lo) & (km < k_hi)
-    keep &= (k[:, None, None].abs() < h) & (k[None, :, None].abs() < h) & (kz[None, None, :] < h)
-    return keep
-
-
 class BandEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, uhat0, plan, k_lo, k_hi, nsteps, checkpoint_every):
-        N = plan.N[0]
         plan.set_initial(0, uhat0.detach())
         plan.step(nsteps)
-        uT = plan.get_state(0)
+        J = plan.band_energy(0, k_lo, k_hi)
         plan.set_initial(0, uhat0.detach())          # the plan keeps u(0) for the backward
-        m = _band(N, k_lo, k_hi, uT.device)
-        w = _weights(N, uT.device)
-        J = 0.5 * ((uT.abs().to(torch.float64) ** 2) * m * w).sum()
         ctx.plan, ctx.args = plan, (k_lo, k_hi, nsteps, checkpoint_every)
-        return J
+        return torch.tensor(J, dtype=torch.float64, device=uhat0.device)
 
     @staticmethod
     def backward(ctx, gJ):

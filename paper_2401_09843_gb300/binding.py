@@ -28,7 +28,7 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
            "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
            "ns3d_set_clock", "ns3d_test_poison_workspaces", "ns3d_vorticity_magnitude",
-           "ns3d_physical_field"]
+           "ns3d_physical_field", "ns3d_band_energy"]
 
 
 class Ns3dError(RuntimeError):
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "ns3d_test_poison_workspaces": (i, [vp]),
         "ns3d_vorticity_magnitude": (i, [vp, i, vp, i]),
         "ns3d_physical_field": (i, [vp, i, vp, i]),
+        "ns3d_band_energy": (i, [vp, i, d, d, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -271,6 +272,13 @@ class Plan:
                                               int(checkpoint_every), ctypes.c_void_p(out.data_ptr()), 1),
                "ns3d_grad_band_energy")
         return out
+
+    def band_energy(self, member: int, k_lo: float, k_hi: float) -> float:
+        """J = 1/2 sum_{k_lo <= |k| < k_hi} |u_hat_k|^2 of the member's state."""
+        J = ctypes.c_double(0.0)
+        _check(self.lib.ns3d_band_energy(self.h, member, float(k_lo), float(k_hi), ctypes.byref(J)),
+               "ns3d_band_energy")
+        return J.value
 
     def ensemble_stats(self, level_N: int, fields: bool = True, ball: bool = True):
         N = int(level_N)

@@ -40,6 +40,66 @@ __global__ void k_band(const cplx<T>* u, cplx<T>* out, int N, double k_lo, doubl
     band_point<T>(u, out, N, k_lo, k_hi, kx, j);
 }
 
+// J = 1/2 sum_{k_lo <= |k| < k_hi} |u_hat_k|^2 over the full spectrum of a
+// state in the plan's compact layout [3][kx N][ky N][kz h], one block per kx
+// plane: each thread sums its points with Neumaier compensation (Knuth's
+// TwoSum of the running sum and each term), then the block merges the
+// threads' pairs by a fixed tree in shared memory, so the result does not
+// depend on scheduling.  part[kx] = (sum, compensation) of the plane.
+struct BandSum {
+  double s, c;
+};
+
+NS3D_HD BandSum band_sum_merge(BandSum a, BandSum b) {
+  const double s = a.s + b.s;
+  const double bp = s - a.s;
+  const double e = (a.s - (s - bp)) + (b.s - bp);
+  return {s, (a.c + b.c) + e};
+}
+
+constexpr int kBandThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kBandThreads) k_band_energy(const cplx<T>* u, int N, double k_lo,
+                                                              double k_hi, double2* part) {
+  __shared__ double ss[kBandThreads], sc[kBandThreads];
+  const int h = N / 2;
+  const int kx = blockIdx.x;
+  const int sx = kx < h ? kx : kx - N;
+  const long long plane = (long long)N * N * h;
+  BandSum acc{0.0, 0.0};
+  if (kx != h) {
+    for (int j = threadIdx.x; j < N * h; j += kBandThreads) {
+      const int kz = j % h, ky = j / h;
+      if (ky == h) continue;
+      const int sy = ky < h ? ky : ky - N;
+      const double km = sqrt((double)(sx * sx + sy * sy + kz * kz));
+      if (!(km >= k_lo && km < k_hi)) continue;
+      const long long off = (long long)kx * N * h + j;
+      double e = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const cplx<T> v = u[c * plane + off];
+        e += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
+      // 1/2 |u_hat_k|^2, twice for kz > 0 (the mirror mode -k)
+      acc = band_sum_merge(acc, BandSum{kz > 0 ? e : 0.5 * e, 0.0});
+    }
+  }
+  ss[threadIdx.x] = acc.s;
+  sc[threadIdx.x] = acc.c;
+  __syncthreads();
+  for (int d = kBandThreads / 2; d > 0; d >>= 1) {
+    if (threadIdx.x < d) {
+      const BandSum r = band_sum_merge(BandSum{ss[threadIdx.x], sc[threadIdx.x]},
+                                       BandSum{ss[threadIdx.x + d], sc[threadIdx.x + d]});
+      ss[threadIdx.x] = r.s;
+      sc[threadIdx.x] = r.c;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[kx] = make_double2(ss[0], sc[0]);
+}
+
 template <typename T>
 __global__ void k_zadj(ZAdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
@@ -319,7 +379,39 @@ ns3d_status grad_impl(ns3d_plan p, const LevelView& L, int idx, double k_lo, dou
   return NS3D_OK;
 }
 
+template <typename T>
+ns3d_status band_energy_impl(ns3d_plan p, const LevelView& L, int idx, double k_lo, double k_hi,
+                             double* J) {
+  cudaStream_t s = p_stream(p);
+  const long long nU = L.g->nU;
+  double2* part = nullptr;
+  NS3D_CUDA(cudaMalloc(&part, (size_t)L.N * sizeof(double2)));
+  k_band_energy<T><<<L.N, kBandThreads, 0, s>>>(static_cast<const cplx<T>*>(L.U0) + (size_t)idx * nU,
+                                                 L.N, k_lo, k_hi, part);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double2> h(L.N);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, (size_t)L.N * sizeof(double2),
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(part);
+  if (e != cudaSuccess) return NS3D_ERR_CUDA;
+  BandSum tot{0.0, 0.0};
+  for (int kx = 0; kx < L.N; ++kx) tot = band_sum_merge(tot, BandSum{h[kx].x, h[kx].y});
+  *J = tot.s + tot.c;
+  return status_of_level(p, L);
+}
+
 }  // namespace
+
+extern "C" ns3d_status ns3d_band_energy(ns3d_plan p, int member, double k_lo, double k_hi,
+                                        double* J) {
+  LevelView L;
+  int idx;
+  if (!p || !J || !(k_hi > k_lo) || !member_view(p, member, &L, &idx)) return NS3D_ERR_INVALID_ARG;
+  PlanDeviceGuard dg(p);
+  return plan_dtype(p) == NS3D_F32 ? band_energy_impl<float>(p, L, idx, k_lo, k_hi, J)
+                                   : band_energy_impl<double>(p, L, idx, k_lo, k_hi, J);
+}
 
 extern "C" ns3d_status ns3d_adjoint_step(ns3d_plan p, int member, const void* lambda_np1,
                                          void* lambda_n, const void* uhat_n, int on_device) {

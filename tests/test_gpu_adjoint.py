@@ -128,3 +128,26 @@ def test_gradient_config4_size(lib):
         fd = (_J_gpu(B, N, B.NS3D_F64, u0 + h * v, nsteps, dt, 8.0, 16.0)
               - _J_gpu(B, N, B.NS3D_F64, u0 - h * v, nsteps, dt, 8.0, 16.0)) / (2 * h)
         assert abs(S.inner(g, v) - fd) < 1e-6 * abs(fd), seed
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-14), ("f32", 1e-14)])
+def test_band_energy_observable(lib, dt, tol):
+    """ns3d_band_energy against the oracle's J on the member's state, for a
+    band that cuts through shells, the whole spectrum (J = E) and an empty
+    band; two calls return the same bits."""
+    from paper_2401_09843_gb300 import binding as B
+    N = 32
+    u = I.random_spectrum(N, seed=31, k0=4.0)
+    p = B.Plan([N, N], B.NS3D_F64 if dt == "f64" else B.NS3D_F32, eps0=1.0, dt_fixed=0.01)
+    p.set_initial(1, u)
+    ref_u = p.get_state(1).cpu().numpy().astype(np.complex128)   # the state as stored (FP32 rounded)
+    for lo, hi in ((2.5, 7.0), (0.0, 1e9), (100.0, 200.0)):
+        J = p.band_energy(1, lo, hi)
+        Jref = A.band_energy(ref_u, lo, hi)
+        assert abs(J - Jref) <= tol * max(Jref, 1e-300), (lo, hi, J, Jref)
+        assert p.band_energy(1, lo, hi) == J
+    assert abs(p.band_energy(1, 0.0, 1e9) - S.energy(ref_u)) < 1e-14 * S.energy(ref_u)
+    assert p.band_energy(0, 0.0, 1e9) == 0.0          # member 0 is still zero
+    with pytest.raises(B.Ns3dError):
+        p.band_energy(1, 5.0, 5.0)
+    p.close()
