@@ -1,10 +1,11 @@
 // Allocation-free evaluation of the time derivative for small grids.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// right-hand side: code that runs while a CUDA graph is being captured on
-// another thread's allocator, real-time or embedded hosts that fix their memory
-// budget at start-up, and plug-in hosts whose allocator must not be re-entered
-// from a callback.  ns3d_eval_rhs_noalloc serves them: it takes the input and
+// right-hand side: real-time or embedded hosts that fix their device memory
+// budget at start-up, plug-in hosts whose allocator must not be re-entered
+// from a callback, and latency-bound loops that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.  ns3d_eval_rhs_noalloc
+// serves them: it takes the input and
 // output buffers from the caller and keeps every intermediate array of the
 // evaluation in one file-scope device array (g_noalloc_scratch below), which
 // every GPU that loads this library holds until the process exits.  It calls no
@@ -31,8 +32,12 @@ constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of the array, looked up once per device.  In host code the
-// name g_noalloc_scratch is only a host-side stand-in, never a device address.
+// Device address of the array, looked up once per device (by the first call
+// on that device, which should therefore come before any stream capture) and
+// kept for the life of the process: a cudaDeviceReset of that device
+// invalidates it, after which this entry point must not be called again.  In
+// host code the name g_noalloc_scratch is only a host-side stand-in, never a
+// device address.
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
@@ -115,10 +120,11 @@ extern "C" ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d
   if (N < 4 || N % 2 || N > kNoAllocMaxN) return NS3D_ERR_INVALID_ARG;
   const ns3d_params& P = *prm;
   if (!(P.L > 0) || !(P.nu >= 0) || !(P.s >= 0.5) || !(P.theta > 0) || !(P.eps0 >= 0) ||
-      !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < 0)
+      !(P.mN_coef >= 0) || (P.q_form != 0 && P.q_form != 1) || P.n_pad < -1)
     return NS3D_ERR_INVALID_ARG;
   if (P.nonlinear_form != 0) return NS3D_ERR_NOT_SUPPORTED;
-  int Pad = P.n_pad ? P.n_pad : default_padded_size(N);
+  // n_pad 0 and -1 both take the smallest 7-smooth size >= 3N/2 (no benchmark here)
+  int Pad = P.n_pad > 0 ? P.n_pad : default_padded_size(N);
   if (2 * Pad < 3 * N || Pad > 3 * kNoAllocMaxN / 2) return NS3D_ERR_INVALID_ARG;
   const int esz = dtype == NS3D_F32 ? 8 : 16;
   Geom g;
