@@ -15,7 +15,8 @@ the timed region starts; every step streams about 18 GB, far above the
 Under torchrun every rank advances its own sample (weak scaling: the Monte
 Carlo ensemble shards with no data-path collective).  Rank 0 prints one JSON
 line.  ``--impl reference`` times the CPU oracle instead (the paper has no
-code to run): each step is one RK3 step of the oracle at 32^3.
+code to run): each step is one RK3 step of the oracle at 16^3, a bounded
+sample of the workload labelled as such in its config.
 """
 from __future__ import annotations
 
@@ -471,37 +472,120 @@ def kernel_bytes(N: int, P: int, esz: int, members: int):
 KINDS = ["inverse_x", "inverse_y", "zpass", "forward_y", "forward_x", "spectral"]
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one ncu
-# capture of the same command on GB300, keyed (kind, N, dtype, members); an entry is removed
-# when its kernel changes after the capture
-NCU_TRAFFIC = {("zpass", 256, "f32", 1): 453.12e6 + 845.53e6}
+# capture of the same command on GB300, keyed (kind, N, dtype, members), with the profiles/
+# file that records the capture; an entry is removed when its kernel changes after the capture
+NCU_TRAFFIC = {("zpass", 256, "f32", 1): (453.12e6 + 845.53e6, "profiles/zpass_256cube_f32.md")}
+
+
+def traffic_entry(kind: str, N: int, dtype: str, members: int):
+    """(bytes, source) of the ncu capture for this kernel and workload, or (None, None)."""
+    return NCU_TRAFFIC.get((kind, N, dtype, members), (None, None))
 
 
 # ----------------------------------------------------------------------------- oracle timing
 
-def oracle_sample_seconds(N: int, steps: int = 1) -> float:
-    """Wall seconds of `steps` oracle RK3 steps at N^3 in a fresh single-threaded process."""
+_ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def _oracle_member_step(args):
+    """Seconds of one oracle RK3 step of member `member` of the N^3 random
+    workload (runs in a pool worker; one thread each)."""
+    N, member = args
+    import ns3d_inputs as I
+    from oracle import solver as S
+    u = I.random_spectrum(N, seed=20240001, member=member)
+    prm = S.Params(eps0=1.0, cfl=0.5)
+    t = time.perf_counter()
+    S.rk3_step(u, prm)
+    return time.perf_counter() - t
+
+
+def oracle_sample_seconds(N: int, steps: int = 1, taylor_green: bool = False) -> float:
+    """Wall seconds of `steps` oracle RK3 steps at N^3 in a fresh single-threaded
+    process: the random-spectrum sample (CFL 0.5), or the Taylor-Green vortex
+    with nu = 0.01 and dt = 0.01 (the 32^3 FP64 case)."""
+    if taylor_green:
+        setup = ("u = I.taylor_green(%d)\n"
+                 "prm = S.Params(nu=0.01, eps0=1.0, dt_fixed=0.01)\n" % N)
+    else:
+        setup = ("u = I.random_spectrum(%d, seed=20240001)\n"
+                 "prm = S.Params(eps0=1.0, cfl=0.5)\n" % N)
     code = (
         "import time, sys; sys.path.insert(0, %r)\n"
         "import ns3d_inputs as I\n"
-        "from oracle import solver as S\n"
-        "u = I.random_spectrum(%d, seed=20240001)\n"
-        "prm = S.Params(eps0=1.0, cfl=0.5)\n"
+        "from oracle import solver as S\n" % ROOT + setup +
         "S.rk3_step(u, prm)\n"
         "t = time.perf_counter()\n"
         "S.integrate(u, prm, %d)\n"
-        "print(time.perf_counter() - t)\n" % (ROOT, N, steps))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        "print(time.perf_counter() - t)\n" % steps)
+    env = dict(os.environ, **_ONE_THREAD)
     out = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, text=True,
                          check=True)
     return float(out.stdout.strip().splitlines()[-1])
 
 
+def oracle_all_cores(N: int, workers: int):
+    """Ensemble throughput of the oracle on all host cores: `workers`
+    single-threaded spawn-started processes, each advancing its own member by
+    one RK3 step (members are independent, Algorithm 1), timed from the first
+    submission to the last result after a warm-up round."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    old = {k: os.environ.get(k) for k in _ONE_THREAD}
+    os.environ.update(_ONE_THREAD)            # inherited by the spawned workers
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            list(ex.map(_oracle_member_step, [(16, m) for m in range(workers)]))   # imports, warm-up
+            t = time.perf_counter()
+            list(ex.map(_oracle_member_step, [(N, m) for m in range(workers)]))
+            return time.perf_counter() - t
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def host_cpu():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, text=True).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model, os.cpu_count() or 1
+
+
 def cpu_baseline():
+    """The FP64 numpy oracle on this host's cores (a reported baseline, not a
+    target): the random-spectrum workload one RK3 step at 64^3 single-threaded
+    and as an ensemble on all cores, and 20 of the 32^3 Taylor-Green case's
+    100 steps single-threaded."""
     N = 64
-    sec = oracle_sample_seconds(N, 1)
-    return {"value": N ** 3 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one SSP-RK3 step of the FP64 numpy oracle at {N}^3 (P = 96), same "
-                      f"initial-data family and parameters, single thread; {sec:.2f} s"}
+    model, ncpu = host_cpu()
+    sec1 = oracle_sample_seconds(N, 1)
+    workers = max(1, ncpu)
+    secw = oracle_all_cores(N, workers)
+    tg_steps = 20
+    sec_tg = oracle_sample_seconds(32, tg_steps, taylor_green=True)
+    return {"value": workers * N ** 3 / secw, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} members of the random-spectrum workload at {N}^3 (P = 96), one "
+                      f"SSP-RK3 step each, one single-threaded process per core, all at once: "
+                      f"{secw:.2f} s wall",
+            "cpu_model": model, "nproc": ncpu,
+            "single_thread": {"value": N ** 3 / sec1, "unit": UNIT, "cores": 1,
+                              "sample": f"one SSP-RK3 step at {N}^3, one thread: {sec1:.2f} s"},
+            "taylor_green_32": {"value": 32 ** 3 * tg_steps / sec_tg, "unit": UNIT, "cores": 1,
+                                "sample": f"{tg_steps} of the 100 fixed steps (dt = 0.01, nu = 0.01) "
+                                          f"of the 32^3 FP64 Taylor-Green case, one thread: "
+                                          f"{sec_tg:.2f} s"},
+            "not_run": "256^3 (one oracle right-hand side takes minutes on one core): the 64^3 "
+                       "sample of the same initial-data family stands for it, per grid point"}
 
 
 def oracle_step_seconds(N: int, warmup: int, steps: int):
@@ -530,14 +614,19 @@ def run_reference(args, rank, world):
     per = oracle_step_seconds(N, args.warmup, args.steps)
     tot = sum(per)
     value = N ** 3 * args.steps / tot
+    model, ncpu = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.N}^3 random-spectrum sample per GPU, CFL 0.5, s=1.5",
-                   "N": args.N, "members_per_gpu": args.members, "l2": "inputs > L2"},
+        "config": {"workload": f"{N}^3 random-spectrum sample (k0 = 4, E = 0.5), CFL 0.5, "
+                               "hyper-viscosity s = 1.5, theta = 1/2: a bounded sample of the "
+                               f"{args.N}^3 workload, same initial-data family and parameters, "
+                               "compared per grid point",
+                   "N": N, "sample_of_N": args.N, "members_per_gpu": 1, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "cpu_model": model, "nproc": ncpu,
                          "sample": f"each step is one SSP-RK3 step of the FP64 numpy oracle at {N}^3 "
                                    "(the paper publishes no code to run), single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -720,7 +809,8 @@ def main():
         "roofline": {"bound": "hbm", "kernel": kinds[dom], "achieved": ach, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
                      "bytes_per_launch": kb[kinds[dom]],
-                     "traffic": NCU_TRAFFIC.get((kinds[dom], N, args.dtype, M))},
+                     "traffic": traffic_entry(kinds[dom], N, args.dtype, M)[0],
+                     "traffic_source": traffic_entry(kinds[dom], N, args.dtype, M)[1]},
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved_GBps": step_bytes / (ms / args.steps * 1e-3) / 1e9,
                           "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},

@@ -61,3 +61,24 @@ def test_reference_arm_json_line():
     e = line["e2e"]
     assert e["value"] == line["value"] and e["unit"] == line["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # the line names the workload it actually times (a 16^3 sample of the main one)
+    assert line["config"]["N"] == 16 and line["config"]["sample_of_N"] == 256
+    assert "16^3" in line["config"]["workload"]
+    assert cb["nproc"] >= 1
+
+
+def test_cpu_baseline_all_cores_pool():
+    """The all-core leg of the CPU baseline: one spawn-started single-threaded
+    process per worker, each advancing its own member; a small case here."""
+    sec = bench.oracle_all_cores(8, 2)
+    assert 0 < sec < 120
+    model, n = bench.host_cpu()
+    assert n >= 1
+
+
+def test_traffic_entry_names_its_capture():
+    b, src = bench.traffic_entry("zpass", 256, "f32", 1)
+    assert (b is None) == (src is None)
+    if src is not None:
+        assert os.path.exists(os.path.join(ROOT, src))
+    assert bench.traffic_entry("zpass", 999, "f32", 1) == (None, None)
