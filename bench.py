@@ -74,10 +74,28 @@ def bench_ensemble(B, torch, steps: int, warmup: int, to_t: float = 0.0):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     pts = sum(N ** 3 for N in Ns)
+    # byte model per level: the four passes of a fused FP32 level (inverse y,
+    # z, forward y, fused x), each member's arrays read and written once per
+    # pass and stage; no reuse through L2 is assumed (the 64^3 level's 256
+    # members hold ~7.7 GB of arrays, far above the 126 MB L2)
+    peak, peak_kind = measured_peaks()
+    levels, step_bytes = {}, 0.0
+    first = 0
+    for N, M, _ in ENSEMBLE_LEVELS:
+        P = plan.info(first)["P"]
+        kb = kernel_bytes(N, P, 8, M)
+        b = 3 * sum(kb[k] for k in ("inverse_y", "zpass", "forward_y", "fused_x"))
+        levels[str(N)] = {"members": M, "P": P, "bytes_per_step": b}
+        step_bytes += b
+        first += M
+    ach = step_bytes / (ms / steps * 1e-3) / 1e9
     info = {"members": {str(N): M for N, M, _ in ENSEMBLE_LEVELS}, "steps": steps,
             "ms_per_step": ms / steps, "value": pts * steps / (ms * 1e-3), "unit": UNIT,
             "samples_steps_per_s": len(Ns) * steps / (ms * 1e-3),
-            "gpu_launches_per_step": plan.info(0)["launches_per_step"]}
+            "gpu_launches_per_step": plan.info(0)["launches_per_step"],
+            "roofline": {"bound": "hbm", "bytes_per_step": step_bytes, "achieved": ach,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                         "levels": levels}}
     if to_t > 0:
         # the workload's horizon: every member to t = to_t (a member stops at it
         # while the others go on), then the FP64 statistics of each level
@@ -352,6 +370,42 @@ def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
     out["f32_gradient_rel_l2_vs_f64"] = float(torch.linalg.vector_norm(d) /
                                               torch.linalg.vector_norm(grads["f64"]))
     return {"N": N, "steps": nsteps, "checkpoint_every": every, **out}
+
+
+def bench_mesh_refinement(B, torch, levels=(64, 128), ref_N: int = 256, members: int = 16,
+                          t_end: float = 0.25):
+    """Mesh refinement of section 6.1: the perturbed Taylor-Green initial
+    measure on the unit torus (s = 1.5, nu = 0), `members` samples at each
+    coarse resolution and at the reference resolution ref_N, all in one FP32
+    plan run to t_end with per-member CFL steps; then, per coarse level, the
+    1-point Wasserstein distance, mean, variance and paired sample errors
+    against the reference on the coarse grid points, with the Monte Carlo
+    error bar of the mean difference (ns3d_mesh_refinement)."""
+    import numpy as np
+    import ns3d_inputs as I
+    Ns = [N for N in tuple(levels) + (ref_N,) for _ in range(members)]
+    plan = B.Plan(Ns, B.NS3D_F32, L=1.0, eps0=1.0, cfl=0.5)
+    for i, N in enumerate(Ns):
+        plan.set_initial(i, I.perturbed_taylor_green(N, seed=20240061, member=i % members))
+        plan.project(i)                   # the flow starts from the divergence-free part
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 20000:
+        plan.step(50, t_end=t_end)
+        steps += 50
+        plan.synchronize()
+        if min(plan.clock(m)[0] for m in range(len(Ns))) >= t_end * (1 - 1e-12):
+            break
+    wall = time.perf_counter() - t0
+    out = {"initial_measure": "perturbed Taylor-Green (section 6.1), L = 1", "members": members,
+           "reference_N": ref_N, "t": t_end, "graph_steps": steps, "wall_s": wall, "dtype": "f32",
+           "levels": {}}
+    for N in levels:
+        r = plan.mesh_refinement(N, ref_N)
+        out["levels"][str(N)] = {k: r[k] for k in ("w1", "mean_err", "var_err", "sample_err", "mc_se")}
+    plan.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def parse():
@@ -827,6 +881,7 @@ def main():
         line["largest"] = bench_largest(B, torch)
         line["cufft_pipeline"] = bench_cufft(torch, N)
         line["adjoint"] = bench_adjoint(B, torch)
+        line["mesh_refinement"] = bench_mesh_refinement(B, torch)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

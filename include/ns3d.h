@@ -136,6 +136,14 @@ ns3d_status ns3d_plan_info(ns3d_plan plan, int member, int* N, int* P, size_t* d
  * time to 0 (initial data u(0) = P_N u0 of eq. shv_disc). */
 ns3d_status ns3d_set_initial(ns3d_plan plan, int member, const void* uhat, int uhat_on_device);
 
+/* Replaces member `member`'s state by its divergence-free part, the Leray
+ * projection (I - kappa kappa^T / |kappa|^2) u_hat_k of section 2.3 at every
+ * k != 0 (the mean flow k = 0 is kept): for initial data that is not
+ * divergence-free, such as the perturbed Taylor-Green and shear-flow measures
+ * of section 6, whose evolution starts from the projected field.  The clock is
+ * unchanged.  Stream-ordered. */
+ns3d_status ns3d_project(ns3d_plan plan, int member);
+
 /* Copies member `member`'s coefficients out (D1 layout, Nyquist planes zero)
  * and, if t_out is not NULL, its time.  Synchronises; returns the member's
  * sticky device status (NONFINITE / UNSTABLE_DT) if one was raised. */
@@ -265,6 +273,40 @@ ns3d_status ns3d_vorticity_magnitude(ns3d_plan plan, int member, void* out, int 
  * resolutions (section 6.1, mesh refinement).  Synchronises.  NOT_SUPPORTED if
  * N has a prime factor above 7. */
 ns3d_status ns3d_physical_field(ns3d_plan plan, int member, void* out, int out_on_device);
+
+/* Mesh-refinement measures of section 6.1 between two levels of the plan: the
+ * coarse level of resolution coarse_N (Ma members) and the fine level fine_N
+ * (Mb members, fine_N a multiple of coarse_N), compared at the coarse grid
+ * points x_j = j L / coarse_N (for the fine fields: their values at those
+ * points), per velocity component c, each averaged over the points:
+ *   w1[c]          1-point Wasserstein distance of the one-point marginals,
+ *                  W1 = integral |F_a(t) - F_b(t)| dt of the empirical CDFs of
+ *                  the Ma coarse and Mb fine values at the point
+ *   mean_err[c]    |mean_a - mean_b| (sample means)
+ *   var_err[c]     |var_a - var_b| (sample variances, divisor M - 1)
+ *   sample_err[c]  mean over members m of |a_m - b_m| (member m of each level
+ *                  drawn from the same sample of the initial measure); -1 when
+ *                  Ma != Mb
+ *   mc_se[c]       sqrt(var_a / Ma + var_b / Mb): the Monte Carlo error bar
+ *                  of the difference of the means, the floor below which
+ *                  mean_err cannot be resolved
+ * Sums are compensated FP64 in a fixed order.  The members' fields are formed
+ * on the device (as ns3d_physical_field); temporary device memory: (Ma + Mb)
+ * x 3 coarse_N^3 values plus one fine field.  Synchronises.  Errors:
+ * INVALID_ARG (no such level, fine_N not a multiple of coarse_N),
+ * NOT_SUPPORTED (more than 128 members in a level, or N with a prime factor
+ * above 7), OUT_OF_MEMORY. */
+typedef struct {
+  double w1[3];
+  double mean_err[3];
+  double var_err[3];
+  double sample_err[3];
+  double mc_se[3];
+  int coarse_members;
+  int fine_members;
+} ns3d_refinement;
+
+ns3d_status ns3d_mesh_refinement(ns3d_plan plan, int coarse_N, int fine_N, ns3d_refinement* out);
 
 /* Diagnostic: advances every member by `nsteps` steps like ns3d_step, but
  * launches the kernels one by one (no graph) with CUDA events recorded on the

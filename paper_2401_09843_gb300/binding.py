@@ -28,7 +28,8 @@ SYMBOLS = ["ns3d_params_default", "ns3d_plan_create", "ns3d_plan_destroy", "ns3d
            "ns3d_ensemble_stats", "ns3d_status_string", "ns3d_step_timed",
            "ns3d_eval_rhs_noalloc", "ns3d_test_stall_staging", "ns3d_get_clock",
            "ns3d_set_clock", "ns3d_test_poison_workspaces", "ns3d_vorticity_magnitude",
-           "ns3d_physical_field", "ns3d_band_energy"]
+           "ns3d_physical_field", "ns3d_band_energy", "ns3d_mesh_refinement",
+           "ns3d_project"]
 
 
 class Ns3dError(RuntimeError):
@@ -55,6 +56,13 @@ class Stats(ctypes.Structure):
                 ("enstrophy", ctypes.c_double), ("enstrophy_se", ctypes.c_double),
                 ("dissipation", ctypes.c_double), ("dissipation_se", ctypes.c_double),
                 ("s2_ball", ctypes.c_void_p), ("s2_ball_se", ctypes.c_void_p)]
+
+
+class Refinement(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_double * 3), ("mean_err", ctypes.c_double * 3),
+                ("var_err", ctypes.c_double * 3), ("sample_err", ctypes.c_double * 3),
+                ("mc_se", ctypes.c_double * 3), ("coarse_members", ctypes.c_int),
+                ("fine_members", ctypes.c_int)]
 
 
 _lib = None
@@ -92,6 +100,8 @@ def load(path: str = LIB_PATH):
         "ns3d_vorticity_magnitude": (i, [vp, i, vp, i]),
         "ns3d_physical_field": (i, [vp, i, vp, i]),
         "ns3d_band_energy": (i, [vp, i, d, d, ctypes.POINTER(d)]),
+        "ns3d_mesh_refinement": (i, [vp, i, i, ctypes.POINTER(Refinement)]),
+        "ns3d_project": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,12 +283,27 @@ class Plan:
                "ns3d_grad_band_energy")
         return out
 
+    def project(self, member: int):
+        """Leray-project the member's state in place (ns3d_project)."""
+        _check(self.lib.ns3d_project(self.h, member), "ns3d_project")
+
     def band_energy(self, member: int, k_lo: float, k_hi: float) -> float:
         """J = 1/2 sum_{k_lo <= |k| < k_hi} |u_hat_k|^2 of the member's state."""
         J = ctypes.c_double(0.0)
         _check(self.lib.ns3d_band_energy(self.h, member, float(k_lo), float(k_hi), ctypes.byref(J)),
                "ns3d_band_energy")
         return J.value
+
+    def mesh_refinement(self, coarse_N: int, fine_N: int) -> dict:
+        """Section 6.1 measures between the levels coarse_N and fine_N, per
+        velocity component (see ns3d_mesh_refinement)."""
+        r = Refinement()
+        _check(self.lib.ns3d_mesh_refinement(self.h, int(coarse_N), int(fine_N), ctypes.byref(r)),
+               "ns3d_mesh_refinement")
+        out = {k: [float(x) for x in getattr(r, k)]
+               for k in ("w1", "mean_err", "var_err", "sample_err", "mc_se")}
+        out["coarse_members"], out["fine_members"] = r.coarse_members, r.fine_members
+        return out
 
     def ensemble_stats(self, level_N: int, fields: bool = True, ball: bool = True):
         N = int(level_N)

@@ -798,6 +798,50 @@ extern "C" ns3d_status ns3d_set_initial(ns3d_plan p, int member, const void* uha
   return NS3D_OK;
 }
 
+namespace {
+
+// Leray projection (I - kappa kappa^T / |kappa|^2) of one member's state in the
+// compact layout [3][kx N][ky N][kz h]; k = 0 is left as it is (the mean flow)
+template <typename T>
+__global__ void k_project(cplx<T>* u, int N, T kscale) {
+  const int h = N / 2;
+  const long long plane = (long long)N * N * h;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(i % h), ky = (int)((i / h) % N), kx = (int)(i / ((long long)N * h));
+    const T k0 = kscale * T(kx < h ? kx : kx - N), k1 = kscale * T(ky < h ? ky : ky - N),
+            k2 = kscale * T(kz);
+    const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+    if (!(kk > T(0))) continue;
+    const cplx<T> a = u[i], b = u[plane + i], c = u[2 * plane + i];
+    const T dr = (k0 * a.x + k1 * b.x + k2 * c.x) / kk, di = (k0 * a.y + k1 * b.y + k2 * c.y) / kk;
+    u[i] = cmake(a.x - k0 * dr, a.y - k0 * di);
+    u[plane + i] = cmake(b.x - k1 * dr, b.y - k1 * di);
+    u[2 * plane + i] = cmake(c.x - k2 * dr, c.y - k2 * di);
+  }
+}
+
+}  // namespace
+
+extern "C" ns3d_status ns3d_project(ns3d_plan p, int member) {
+  Level* L;
+  int idx;
+  ns3d_status st = member_lookup(p, member, &L, &idx);
+  if (st != NS3D_OK) return st;
+  DeviceGuard dg(p->device);
+  const long long plane = (long long)L->g.N * L->g.N * L->g.h;
+  const int grid = (int)std::min<long long>((plane + 255) / 256, 152 * 8);
+  if (p->dtype == NS3D_F32)
+    k_project<float><<<grid, 256, 0, p->stream>>>(static_cast<cplx<float>*>(L->U0) + idx * L->g.nU,
+                                                   L->g.N, (float)L->sp.kscale);
+  else
+    k_project<double><<<grid, 256, 0, p->stream>>>(static_cast<cplx<double>*>(L->U0) + idx * L->g.nU,
+                                                    L->g.N, L->sp.kscale);
+  NS3D_CK(cudaGetLastError());
+  L->a_valid = false;
+  return NS3D_OK;
+}
+
 extern "C" ns3d_status ns3d_get_state(ns3d_plan p, int member, void* out, int on_device,
                                       double* t_out) {
   Level* L;

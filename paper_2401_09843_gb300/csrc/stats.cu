@@ -576,6 +576,190 @@ ns3d_status physical_impl(ns3d_plan p, const LevelView& L, int idx, void* out, i
   return ok ? NS3D_OK : NS3D_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------- mesh refinement
+// Section 6.1 compares ensembles of one initial measure at two resolutions
+// pointwise on the coarse grid x_j = j L / Nc (the fine grid's points with
+// index r j, r = Nf / Nc): the error of each sample, of the mean and of the
+// variance, and the 1-point Wasserstein distance of the one-point marginals,
+// W1(a, b) = integral |F_a(t) - F_b(t)| dt between the empirical CDFs of the
+// Ma coarse and Mb fine values at the point, all averaged over the points.
+
+constexpr int kRefineMaxM = 128;    // members per level (values kept per thread)
+constexpr int kRefineThreads = 128;
+constexpr int kRefineStats = 5;     // W1, |mean diff|, |var diff|, sample error, MC error bar
+
+// fine samples on the coarse points: out[c][j] = in[c][r j] for the three components
+template <typename T>
+__global__ void k_subsample(const T* in, T* out, int Nf, int Nc) {
+  const int r = Nf / Nc;
+  const long long n3 = (long long)Nc * Nc * Nc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / n3);
+    const long long j = i % n3;
+    const long long x = j / ((long long)Nc * Nc), y = (j / Nc) % Nc, z = j % Nc;
+    out[i] = in[(long long)c * Nf * Nf * Nf + ((x * r) * Nf + y * r) * Nf + z * r];
+  }
+}
+
+__device__ void refine_sort(double* v, int n) {   // insertion sort (n <= kRefineMaxM)
+  for (int i = 1; i < n; ++i) {
+    const double x = v[i];
+    int j = i - 1;
+    while (j >= 0 && v[j] > x) {
+      v[j + 1] = v[j];
+      --j;
+    }
+    v[j + 1] = x;
+  }
+}
+
+// samples [M][3][n3] (plan dtype); block (b, c) reduces its points of component
+// c into part[(c * gridDim.x + b) * kRefineStats + s] as compensated pairs
+template <typename T>
+__global__ void __launch_bounds__(kRefineThreads) k_refine(const T* sa, int Ma, const T* sb, int Mb,
+                                                           long long n3, double2* part) {
+  __shared__ double ss[kRefineStats][kRefineThreads], sc[kRefineStats][kRefineThreads];
+  const int c = blockIdx.y;
+  CSum acc[kRefineStats];
+  for (int q = 0; q < kRefineStats; ++q) acc[q] = CSum{0.0, 0.0};
+  double a[kRefineMaxM], b[kRefineMaxM];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n3;
+       j += (long long)gridDim.x * blockDim.x) {
+    double ma = 0.0, mb = 0.0, se = 0.0;
+    for (int m = 0; m < Ma; ++m) {
+      a[m] = (double)sa[((long long)m * 3 + c) * n3 + j];
+      ma += a[m];
+    }
+    for (int m = 0; m < Mb; ++m) {
+      b[m] = (double)sb[((long long)m * 3 + c) * n3 + j];
+      mb += b[m];
+    }
+    if (Ma == Mb) {
+      for (int m = 0; m < Ma; ++m) se += fabs(a[m] - b[m]);
+      se /= Ma;
+    }
+    ma /= Ma;
+    mb /= Mb;
+    double va = 0.0, vb = 0.0;     // two-pass variances (divisor M - 1)
+    for (int m = 0; m < Ma; ++m) va += (a[m] - ma) * (a[m] - ma);
+    for (int m = 0; m < Mb; ++m) vb += (b[m] - mb) * (b[m] - mb);
+    va = Ma > 1 ? va / (Ma - 1) : 0.0;
+    vb = Mb > 1 ? vb / (Mb - 1) : 0.0;
+    refine_sort(a, Ma);
+    refine_sort(b, Mb);
+    // integral of |F_a - F_b| over the merged sorted values
+    double w = 0.0, prev = a[0] < b[0] ? a[0] : b[0];
+    int ia = 0, ib = 0;
+    while (ia < Ma || ib < Mb) {
+      const bool takea = ib >= Mb || (ia < Ma && a[ia] <= b[ib]);
+      const double x = takea ? a[ia] : b[ib];
+      w += fabs((double)ia / Ma - (double)ib / Mb) * (x - prev);
+      prev = x;
+      if (takea) ++ia; else ++ib;
+    }
+    acc[0] = csum_merge(acc[0], CSum{w, 0.0});
+    acc[1] = csum_merge(acc[1], CSum{fabs(ma - mb), 0.0});
+    acc[2] = csum_merge(acc[2], CSum{fabs(va - vb), 0.0});
+    acc[3] = csum_merge(acc[3], CSum{se, 0.0});
+    acc[4] = csum_merge(acc[4], CSum{sqrt(va / Ma + vb / Mb), 0.0});
+  }
+  for (int q = 0; q < kRefineStats; ++q) {
+    ss[q][threadIdx.x] = acc[q].s;
+    sc[q][threadIdx.x] = acc[q].c;
+  }
+  __syncthreads();
+  for (int d = kRefineThreads / 2; d > 0; d >>= 1) {
+    if (threadIdx.x < d)
+      for (int q = 0; q < kRefineStats; ++q) {
+        const CSum r = csum_merge(CSum{ss[q][threadIdx.x], sc[q][threadIdx.x]},
+                                  CSum{ss[q][threadIdx.x + d], sc[q][threadIdx.x + d]});
+        ss[q][threadIdx.x] = r.s;
+        sc[q][threadIdx.x] = r.c;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kRefineStats; ++q)
+      part[((long long)c * gridDim.x + blockIdx.x) * kRefineStats + q] = make_double2(ss[q][0], sc[q][0]);
+}
+
+template <typename T>
+ns3d_status physical_impl(ns3d_plan p, const LevelView& L, int idx, void* out, int on_device,
+                          int what);
+
+template <typename T>
+ns3d_status refine_impl(ns3d_plan p, const LevelView& Lc, const LevelView& Lf, ns3d_refinement* out) {
+  const int Nc = Lc.N, Nf = Lf.N, Ma = Lc.B, Mb = Lf.B;
+  const long long n3 = (long long)Nc * Nc * Nc, nf3 = (long long)Nf * Nf * Nf;
+  cudaStream_t s = p_stream(p);
+  std::vector<void*> tmp;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    tmp.push_back(q);
+    return q;
+  };
+  auto cleanup = [&]() {
+    for (void* q : tmp) cudaFree(q);
+  };
+  T* sa = static_cast<T*>(alloc(sizeof(T) * 3 * n3 * Ma));
+  T* sb = static_cast<T*>(alloc(sizeof(T) * 3 * n3 * Mb));
+  T* fine = Nf != Nc ? static_cast<T*>(alloc(sizeof(T) * 3 * nf3)) : nullptr;
+  const int nb = (int)std::min<long long>((n3 + kRefineThreads - 1) / kRefineThreads, 152 * 4);
+  double2* part = static_cast<double2*>(alloc(sizeof(double2) * 3 * nb * kRefineStats));
+  if (!sa || !sb || (Nf != Nc && !fine) || !part) {
+    cleanup();
+    return NS3D_ERR_OUT_OF_MEMORY;
+  }
+  ns3d_status st = NS3D_OK;
+  for (int m = 0; m < Ma && st == NS3D_OK; ++m)
+    st = physical_impl<T>(p, Lc, m, sa + 3 * n3 * m, 1, 0);
+  for (int m = 0; m < Mb && st == NS3D_OK; ++m) {
+    if (Nf == Nc) {
+      st = physical_impl<T>(p, Lf, m, sb + 3 * n3 * m, 1, 0);
+    } else {
+      st = physical_impl<T>(p, Lf, m, fine, 1, 0);
+      if (st == NS3D_OK) {
+        k_subsample<T><<<grid_of(3 * n3), 256, 0, s>>>(fine, sb + 3 * n3 * m, Nf, Nc);
+        if (cudaGetLastError() != cudaSuccess) st = NS3D_ERR_CUDA;
+      }
+    }
+  }
+  std::vector<double2> h(3 * (size_t)nb * kRefineStats);
+  if (st == NS3D_OK) {
+    k_refine<T><<<dim3(nb, 3), kRefineThreads, 0, s>>>(sa, Ma, sb, Mb, n3, part);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h.data(), part, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      st = NS3D_ERR_CUDA;
+  }
+  cleanup();
+  if (st != NS3D_OK) return st;
+  for (int c = 0; c < 3; ++c) {
+    double v[kRefineStats];
+    for (int q = 0; q < kRefineStats; ++q) {
+      CSum a{0.0, 0.0};
+      for (int b = 0; b < nb; ++b) {
+        const double2 x = h[((size_t)c * nb + b) * kRefineStats + q];
+        a = csum_merge(a, CSum{x.x, x.y});
+      }
+      v[q] = (a.s + a.c) / (double)n3;
+    }
+    out->w1[c] = v[0];
+    out->mean_err[c] = v[1];
+    out->var_err[c] = v[2];
+    out->sample_err[c] = Ma == Mb ? v[3] : -1.0;
+    out->mc_se[c] = v[4];
+  }
+  out->coarse_members = Ma;
+  out->fine_members = Mb;
+  return status_of_level(p, Lc) != NS3D_OK ? status_of_level(p, Lc) : status_of_level(p, Lf);
+}
+
 ns3d_status physical_entry(ns3d_plan p, int member, void* out, int on_device, int what) {
   if (!p || !out) return NS3D_ERR_INVALID_ARG;
   LevelView L;
@@ -594,6 +778,17 @@ extern "C" ns3d_status ns3d_vorticity_magnitude(ns3d_plan p, int member, void* o
 
 extern "C" ns3d_status ns3d_physical_field(ns3d_plan p, int member, void* out, int on_device) {
   return physical_entry(p, member, out, on_device, 0);
+}
+
+extern "C" ns3d_status ns3d_mesh_refinement(ns3d_plan p, int coarse_N, int fine_N,
+                                            ns3d_refinement* out) {
+  if (!p || !out || coarse_N <= 0 || fine_N < coarse_N || fine_N % coarse_N) return NS3D_ERR_INVALID_ARG;
+  LevelView Lc, Lf;
+  if (!find_level(p, coarse_N, &Lc) || !find_level(p, fine_N, &Lf)) return NS3D_ERR_INVALID_ARG;
+  if (Lc.B > kRefineMaxM || Lf.B > kRefineMaxM) return NS3D_ERR_NOT_SUPPORTED;
+  PlanDeviceGuard dg(p);
+  return plan_dtype(p) == NS3D_F32 ? refine_impl<float>(p, Lc, Lf, out)
+                                   : refine_impl<double>(p, Lc, Lf, out);
 }
 
 extern "C" ns3d_status ns3d_ensemble_stats(ns3d_plan p, int level_N, ns3d_stats* out) {

@@ -397,3 +397,27 @@ def test_fp32_and_fp64_statistics_over_500_steps(B):
         assert abs(a[k] - b[k]) < 1e-2 * b[k], k
     sa, sb = np.asarray(a["spectrum"])[1:33], np.asarray(b["spectrum"])[1:33]
     assert np.max(np.abs(sa - sb) / sb) < 5e-2
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_project_state_matches_oracle_leray(B, dt):
+    """ns3d_project leaves the divergence-free part of a member's state (the
+    perturbed Taylor-Green data of section 6.1 are not divergence-free) and
+    keeps the mean flow; other members are untouched."""
+    N = 24
+    dtype = B.NS3D_F64 if dt == "f64" else B.NS3D_F32
+    u = I.perturbed_taylor_green(N, seed=5, member=1)
+    u[:, 0, 0, 0] = [0.1, -0.2, 0.3]
+    p = plan(B, [N, N], dtype, L=1.0)
+    p.set_initial(0, u)
+    p.set_initial(1, u)
+    p.project(0)
+    got = p.get_state(0).cpu().numpy().astype(np.complex128)
+    ref = S.leray(u, 1.0)
+    ref[:, 0, 0, 0] = u[:, 0, 0, 0]
+    ref = ref * S.retained_mask(N)
+    assert rel(got, ref) < (1e-14 if dt == "f64" else 1e-6)
+    assert S.divergence_ratio(got, 1.0) < (1e-14 if dt == "f64" else 1e-6)
+    other = p.get_state(1).cpu().numpy().astype(np.complex128)
+    assert rel(other, u * S.retained_mask(N)) < (1e-15 if dt == "f64" else 1e-7)
+    p.close()

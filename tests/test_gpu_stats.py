@@ -226,3 +226,46 @@ def test_spectra_are_compensated_and_reproducible(lib, N):
     assert np.all(np.abs(np.asarray(a["enstrophy_spectrum"]) - zspec) <= tol * zspec)
     assert abs(a["energy"] - math.fsum(ev)) <= tol * math.fsum(ev)
     assert abs(a["enstrophy"] - math.fsum(zv)) <= tol * math.fsum(zv)
+
+
+@pytest.mark.parametrize("Ma,Mb", [(6, 6), (5, 7)])
+def test_mesh_refinement_measures_on_the_gpu(lib, Ma, Mb):
+    """ns3d_mesh_refinement between a 16^3 and a 32^3 level of one plan
+    (perturbed Taylor-Green samples of section 6.1, FP64, a few steps) against
+    the oracle's definitions on the oracle's own fields: the 1-point
+    Wasserstein distance (integral of |F_a - F_b| per point), the mean,
+    variance and (equal counts) paired sample errors and the MC error bar,
+    per component, averaged over the coarse points."""
+    from paper_2401_09843_gb300 import binding as B
+    dt, n = 2e-4, 4
+    prm = S.Params(L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+    Ns = [16] * Ma + [32] * Mb
+    u0 = [S.leray(I.perturbed_taylor_green(N, seed=611, member=m if m < Ma else m - Ma), 1.0)
+          for m, N in enumerate(Ns)]
+    p = B.Plan(Ns, B.NS3D_F64, L=1.0, eps0=1.0, nu=1e-3, dt_fixed=dt)
+    for m, x in enumerate(u0):
+        p.set_initial(m, x)
+    p.step(n)
+    got = p.mesh_refinement(16, 32)
+    p.close()
+    f = [T.physical_on_grid(S.integrate(x, prm, n)[0]) for x in u0]
+    a = np.stack(f[:Ma])                                  # (Ma, 3, 16, 16, 16)
+    b = np.stack(f[Ma:])[:, :, ::2, ::2, ::2]             # fine values at the coarse points
+    assert got["coarse_members"] == Ma and got["fine_members"] == Mb
+    for c in range(3):
+        w = T.wasserstein1_one_point(a[:, c], b[:, c])
+        assert abs(got["w1"][c] - w) < 1e-10 * w + 1e-15, (c, got["w1"][c], w)
+        me = np.mean(np.abs(a[:, c].mean(0) - b[:, c].mean(0)))
+        va, vb = a[:, c].var(0, ddof=1), b[:, c].var(0, ddof=1)
+        ve = np.mean(np.abs(va - vb))
+        se = np.mean(np.sqrt(va / Ma + vb / Mb))
+        assert abs(got["mean_err"][c] - me) < 1e-10 * me + 1e-15
+        assert abs(got["var_err"][c] - ve) < 1e-9 * ve + 1e-15
+        assert abs(got["mc_se"][c] - se) < 1e-10 * se
+        if Ma == Mb:
+            sp = np.mean(np.abs(a[:, c] - b[:, c]))
+            assert abs(got["sample_err"][c] - sp) < 1e-10 * sp
+            assert got["mean_err"][c] <= got["w1"][c] + 1e-15 <= sp + 2e-15
+        else:
+            assert got["sample_err"][c] == -1.0
+        assert got["w1"][c] > 0
