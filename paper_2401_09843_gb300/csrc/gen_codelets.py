@@ -1,4 +1,4 @@
-"""Writes codelets.cuh and codelets_packed.cuh: straight-line small DFTs in registers.
+"""Writes codelets.cuh: straight-line small DFTs in registers.
 
 Run once after editing this file (the output is committed):
     python paper_2401_09843_gb300/csrc/gen_codelets.py
@@ -158,193 +158,5 @@ def main():
         f.write("\n".join(out) + "\n")
 
 
-# ---------------------------------------------------------------------------
-# Packed codelets: the same splittings, written with explicit operations on a
-# lane type V so that two independent transforms run in lockstep (V a pair of
-# floats on the GPU: one add, multiply or fused multiply-add instruction acts
-# on both lanes).  Signs are carried symbolically and folded into the next
-# add/sub or constant, so a negation costs an instruction only where an output
-# is left negated.
-
-class PVal:
-    __slots__ = ("name", "neg")
-
-    def __init__(self, name: str, neg: bool = False):
-        self.name = name
-        self.neg = neg
-
-    def flip(self):
-        return PVal(self.name, not self.neg)
-
-
-class GenP:
-    def __init__(self):
-        self.lines = []
-        self.n = 0
-
-    def _new(self, expr: str, neg: bool = False) -> PVal:
-        k = self.n
-        self.n += 1
-        self.lines.append(f"    const V p{k} = {expr};")
-        return PVal(f"p{k}", neg)
-
-    def radd(self, a: PVal, b: PVal, sub: bool = False) -> PVal:
-        """a + b (or a - b) of real lane values."""
-        bn = b.neg ^ sub
-        if not a.neg and not bn:
-            return self._new(f"padd({a.name}, {b.name})")
-        if not a.neg and bn:
-            return self._new(f"psub({a.name}, {b.name})")
-        if a.neg and not bn:
-            return self._new(f"psub({b.name}, {a.name})")
-        return self._new(f"padd({a.name}, {b.name})", neg=True)
-
-    def rmul(self, c, a: PVal) -> PVal:
-        c = -c if a.neg else c
-        return self._new(f"pmul({plit(c)}, {a.name})")
-
-    def rfma(self, c, a: PVal, acc: PVal) -> PVal:
-        """c a + acc."""
-        c = -c if a.neg else c
-        if acc.neg:   # c a - x = -((-c) a + x)
-            return self._new(f"pfma({plit(-c)}, {a.name}, {acc.name})", neg=True)
-        return self._new(f"pfma({plit(c)}, {a.name}, {acc.name})")
-
-    def lin(self, terms, base: PVal | None = None) -> PVal:
-        """base + sum c_j a_j as a chain of fused multiply-adds."""
-        acc = base
-        for c, a in terms:
-            acc = self.rmul(c, a) if acc is None else self.rfma(c, a, acc)
-        return acc
-
-    def cadd(self, x, y):
-        return (self.radd(x[0], y[0]), self.radd(x[1], y[1]))
-
-    def csub(self, x, y):
-        return (self.radd(x[0], y[0], True), self.radd(x[1], y[1], True))
-
-    def times_i(self, x, s: int):
-        return (x[1].flip(), x[0]) if s > 0 else (x[1], x[0].flip())
-
-    def twiddle(self, x, e: int, R: int, sign: int):
-        e %= R
-        if e == 0:
-            return x
-        if 4 * e == R:
-            return self.times_i(x, sign)
-        if 2 * e == R:
-            return (x[0].flip(), x[1].flip())
-        if 4 * e == 3 * R:
-            return self.times_i(x, -sign)
-        ang = 2 * mpmath.pi * e / R
-        c = mpmath.cos(ang)
-        s = sign * mpmath.sin(ang)
-        re = self.rfma(-s, x[1], self.rmul(c, x[0]))
-        im = self.rfma(s, x[0], self.rmul(c, x[1]))
-        return (re, im)
-
-
-def plit(v) -> str:
-    s = mpmath.nstr(mpmath.mpf(v), 30, strip_zeros=False)
-    return f"pk<V>({s})"
-
-
-def dftp(g: GenP, xs, sign: int):
-    R = len(xs)
-    if R == 1:
-        return list(xs)
-    if R == 2:
-        return [g.cadd(xs[0], xs[1]), g.csub(xs[0], xs[1])]
-    if R == 3:
-        t1 = g.cadd(xs[1], xs[2])
-        t2 = (g.rfma(mpmath.mpf(-0.5), t1[0], xs[0][0]), g.rfma(mpmath.mpf(-0.5), t1[1], xs[0][1]))
-        d = g.csub(xs[1], xs[2])
-        m = sign * mpmath.sin(2 * mpmath.pi / 3)
-        y0 = g.cadd(xs[0], t1)
-        y1 = (g.rfma(-m, d[1], t2[0]), g.rfma(m, d[0], t2[1]))
-        y2 = (g.rfma(m, d[1], t2[0]), g.rfma(-m, d[0], t2[1]))
-        return [y0, y1, y2]
-    if R == 4:
-        a = g.cadd(xs[0], xs[2])
-        b = g.csub(xs[0], xs[2])
-        c = g.cadd(xs[1], xs[3])
-        d = g.csub(xs[1], xs[3])
-        id_ = g.times_i(d, sign)
-        return [g.cadd(a, c), g.cadd(b, id_), g.csub(a, c), g.csub(b, id_)]
-    if R in (5, 7):
-        h = (R - 1) // 2
-        p = [g.cadd(xs[j], xs[R - j]) for j in range(1, h + 1)]
-        q = [g.csub(xs[j], xs[R - j]) for j in range(1, h + 1)]
-        out = [None] * R
-        s0 = xs[0]
-        for pj in p:
-            s0 = g.cadd(s0, pj)
-        out[0] = s0
-        for k in range(1, h + 1):
-            cr = [mpmath.cos(2 * mpmath.pi * j * k / R) for j in range(1, h + 1)]
-            sr = [sign * mpmath.sin(2 * mpmath.pi * j * k / R) for j in range(1, h + 1)]
-            A = (g.lin([(c, pj[0]) for c, pj in zip(cr, p)], xs[0][0]),
-                 g.lin([(c, pj[1]) for c, pj in zip(cr, p)], xs[0][1]))
-            B = (g.lin([(s, qj[0]) for s, qj in zip(sr, q)]),
-                 g.lin([(s, qj[1]) for s, qj in zip(sr, q)]))
-            out[k] = (g.radd(A[0], B[1], True), g.radd(A[1], B[0]))
-            out[R - k] = (g.radd(A[0], B[1]), g.radd(A[1], B[0], True))
-        return out
-    for p in (4, 2, 3, 5, 7):
-        if R % p == 0 and R != p:
-            break
-    m = R // p
-    Y = []
-    for j2 in range(m):
-        sub = dftp(g, [xs[m * j1 + j2] for j1 in range(p)], sign)
-        Y.append([g.twiddle(sub[k1], j2 * k1, R, sign) for k1 in range(p)])
-    X = [None] * R
-    for k1 in range(p):
-        Z = dftp(g, [Y[j2][k1] for j2 in range(m)], sign)
-        for k2 in range(m):
-            X[k1 + p * k2] = Z[k2]
-    return X
-
-
-def emitp(R: int, sign: int) -> str:
-    g = GenP()
-    xs = [(PVal(f"r[{j}]"), PVal(f"i[{j}]")) for j in range(R)]
-    # inputs are read once into named values so that outputs may overwrite r, i
-    g.lines += [f"    const V x{j}r = r[{j}]; const V x{j}i = i[{j}];" for j in range(R)]
-    xs = [(PVal(f"x{j}r"), PVal(f"x{j}i")) for j in range(R)]
-    ys = dftp(g, xs, sign)
-    body = list(g.lines)
-    tail = []
-    for k in range(R):
-        for part, arr in ((ys[k][0], "r"), (ys[k][1], "i")):
-            expr = f"pneg({part.name})" if part.neg else part.name
-            tail.append(f"    {arr}[{k}] = {expr};")
-    head = [f"template <> struct DftP<{R}, {sign}> {{",
-            "  template <typename V>",
-            "  static NS3D_HD void run(V* r, V* i) {"]
-    return "\n".join(head + body + tail + ["  }", "};", ""])
-
-
-def main_packed():
-    out = ["// Generated by gen_codelets.py: packed in-register DFTs with literal twiddles.",
-           "// X[k] = sum_j x[j] exp(SIGN 2 pi i j k / R) on real and imaginary lane arrays",
-           "// r[], i[] of a lane type V (padd/psub/pmul/pfma/pneg/pk<V> overloads): for V a",
-           "// float pair, two transforms run in lockstep.  SIGN = -1 forward, +1 inverse.",
-           "#pragma once",
-           "",
-           "template <int R, int SIGN> struct DftP;",
-           "template <int SIGN> struct DftP<1, SIGN> {",
-           "  template <typename V> static NS3D_HD void run(V*, V*) {}",
-           "};",
-           ""]
-    for R in RADICES:
-        for sign in (-1, 1):
-            out.append(emitp(R, sign))
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "codelets_packed.cuh")
-    with open(path, "w") as f:
-        f.write("\n".join(out) + "\n")
-
-
 if __name__ == "__main__":
     main()
-    main_packed()

@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <cstring>
 #include <limits>
-#include <type_traits>
 #include <vector>
 
 #include "ns3d_geom.h"
@@ -17,7 +16,6 @@
 #include "ns3d_colfast3.cuh"
 #include "ns3d_zfast3.cuh"
 #include "ns3d_zrot.cuh"
-#include "ns3d_packed.cuh"
 
 namespace {
 
@@ -609,33 +607,6 @@ int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
   run_zfast3<float, 16, 12, 8>(a, 1, nx);
   std::memcpy(umax, &ctrl.umax_bits, sizeof(double));
   return ctrl.status;
-}
-
-// Packed codelet DftP<R, sign> on the host: lanes = 2 runs it on pf2 (two
-// transforms in lockstep; re, im hold R pairs (x, y) each), lanes = 1 on float.
-// Returns -1 for a radix without a codelet.
-int ns3d_hostcheck_dftp(int R, int sign, int lanes, float* re, float* im) {
-  bool done = false;
-  auto go = [&](auto tag) {
-    constexpr int RR = decltype(tag)::value;
-    if (RR != R) return;
-    done = true;
-    if (lanes == 2) {
-      pf2* r = reinterpret_cast<pf2*>(re);
-      pf2* i = reinterpret_cast<pf2*>(im);
-      if (sign < 0) DftP<RR, -1>::run(r, i); else DftP<RR, 1>::run(r, i);
-    } else {
-      if (sign < 0) DftP<RR, -1>::run(re, im); else DftP<RR, 1>::run(re, im);
-    }
-  };
-#define NS3D_HC_DFTP(r) go(std::integral_constant<int, r>{});
-  NS3D_HC_DFTP(2) NS3D_HC_DFTP(3) NS3D_HC_DFTP(4) NS3D_HC_DFTP(5) NS3D_HC_DFTP(6)
-  NS3D_HC_DFTP(7) NS3D_HC_DFTP(8) NS3D_HC_DFTP(9) NS3D_HC_DFTP(10) NS3D_HC_DFTP(12)
-  NS3D_HC_DFTP(14) NS3D_HC_DFTP(15) NS3D_HC_DFTP(16) NS3D_HC_DFTP(18) NS3D_HC_DFTP(20)
-  NS3D_HC_DFTP(21) NS3D_HC_DFTP(24) NS3D_HC_DFTP(25) NS3D_HC_DFTP(27) NS3D_HC_DFTP(28)
-  NS3D_HC_DFTP(32)
-#undef NS3D_HC_DFTP
-  return done ? 0 : -1;
 }
 
 // Radix plan chosen for length n (for tests).

@@ -97,49 +97,73 @@ NS3D_HD void zfast_load_twiddles(const ZFastCtx<T, N1, N2>& c, int tid, int nthr
   }
 }
 
-// inverse pass 1: tasks (pair g, line l, j2), j2 fastest for coalesced loads
+// inverse pass 1, task t = (pair g, line l, j2), j2 fastest for coalesced
+// loads: the N1 inputs of the task from global memory (padding band known at
+// compile time) ...
 template <typename T, int N1, int N2>
-NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+NS3D_HD void zfast_inv1_load(const ZFastCtx<T, N1, N2>& c, int t, cplx<T>* v) {
   using S = ZFastShape<N1, N2>;
   const ZArgs<T>& a = *c.a;
   constexpr int h = S::H;
   const cplx<T>* in = a.in + c.bz * a.in_bs + c.by * a.xs + (long long)c.y0 * h;
-  for (int t = tid; t < S::NPAIR * 3 * N2; t += nthr) {
-    const int j2 = t % N2;
-    const int l = (t / N2) % 3;
-    const int g = t / (3 * N2);
-    const int ca = 2 * g + (l == 1 ? 1 : 0);
-    const int cb = 2 * g + (l == 0 ? 0 : 1);
-    const cplx<T>* ia = in + (l == 2 ? 2 : 0) * a.in_cs;
-    const cplx<T>* ib = in + (l == 2 ? 2 : 1) * a.in_cs;
-    cplx<T> v[N1];
-    const bool full = (S::P % S::Y == 0);     // every tile has Y columns
+  const int j2 = t % N2;
+  const int l = (t / N2) % 3;
+  const int g = t / (3 * N2);
+  const int ca = 2 * g + (l == 1 ? 1 : 0);
+  const int cb = 2 * g + (l == 0 ? 0 : 1);
+  const cplx<T>* ia = in + (l == 2 ? 2 : 0) * a.in_cs;
+  const cplx<T>* ib = in + (l == 2 ? 2 : 1) * a.in_cs;
+  const bool full = (S::P % S::Y == 0);     // every tile has Y columns
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) {
-      // positions N2 j1 .. N2 j1 + N2 - 1: the zero band is known at compile time
-      const int p = N2 * j1 + j2;
-      const int reg = pad_region(N2 * j1, N2, S::P, S::H);
-      if (reg == PAD_ZERO) {
-        v[j1] = czero<T>();
-      } else if (full && reg == PAD_LOW) {          // u_a[p] + i u_b[p]
-        cplx<T> x = ia[ca * h + p], y = ib[cb * h + p];
-        if (j1 == 0 && p == 0) {
-          x.y = T(0);
-          y.y = T(0);
-        }
-        v[j1] = cmake(x.x - y.y, x.y + y.x);
-      } else if (full && reg == PAD_HIGH) {         // conj(u_a[P-p]) + i conj(u_b[P-p])
-        const cplx<T> x = ia[ca * h + (S::P - p)], y = ib[cb * h + (S::P - p)];
-        v[j1] = cmake(x.x + y.y, -x.y + y.x);
-      } else {
-        v[j1] = pack2(ia, ib, S::P, S::H, p, ca, cb, c.ncol);
+  for (int j1 = 0; j1 < N1; ++j1) {
+    // positions N2 j1 .. N2 j1 + N2 - 1: the zero band is known at compile time
+    const int p = N2 * j1 + j2;
+    const int reg = pad_region(N2 * j1, N2, S::P, S::H);
+    if (reg == PAD_ZERO) {
+      v[j1] = czero<T>();
+    } else if (full && reg == PAD_LOW) {          // u_a[p] + i u_b[p]
+      cplx<T> x = ia[ca * h + p], y = ib[cb * h + p];
+      if (j1 == 0 && p == 0) {
+        x.y = T(0);
+        y.y = T(0);
       }
+      v[j1] = cmake(x.x - y.y, x.y + y.x);
+    } else if (full && reg == PAD_HIGH) {         // conj(u_a[P-p]) + i conj(u_b[P-p])
+      const cplx<T> x = ia[ca * h + (S::P - p)], y = ib[cb * h + (S::P - p)];
+      v[j1] = cmake(x.x + y.y, -x.y + y.x);
+    } else {
+      v[j1] = pack2(ia, ib, S::P, S::H, p, ca, cb, c.ncol);
     }
-    Dft<N1, +1>::run(v);
-    cplx<T>* X = c.X + (g * 3 + l) * S::LP;
+  }
+}
+
+// ... and its radix-N1 DFT, twiddle and store to the exchange buffer
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_inv1_finish(const ZFastCtx<T, N1, N2>& c, int t, cplx<T>* v) {
+  using S = ZFastShape<N1, N2>;
+  const int j2 = t % N2;
+  const int l = (t / N2) % 3;
+  const int g = t / (3 * N2);
+  Dft<N1, +1>::run(v);
+  cplx<T>* X = c.X + (g * 3 + l) * S::LP;
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1)
-      X[j2 * (N1 + 1) + k1] = k1 == 0 ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];   // twi[k1 N2] = 1
+  for (int k1 = 0; k1 < N1; ++k1)
+    X[j2 * (N1 + 1) + k1] = k1 == 0 ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];   // twi[k1 N2] = 1
+}
+
+// inverse pass 1: each thread takes tasks t and t + nthr at a time and issues
+// the global loads of both before either transform, so that one task's load
+// latency overlaps the other's (the task count is a multiple of 2 nthr)
+template <typename T, int N1, int N2>
+NS3D_HD void zfast_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+  using S = ZFastShape<N1, N2>;
+  static_assert((S::NPAIR * 3 * N2) % (2 * S::NTHR) == 0, "tasks in pairs of thread sweeps");
+  for (int t = tid; t < S::NPAIR * 3 * N2; t += 2 * nthr) {
+    cplx<T> va[N1], vb[N1];
+    zfast_inv1_load<T, N1, N2>(c, t, va);
+    zfast_inv1_load<T, N1, N2>(c, t + nthr, vb);
+    zfast_inv1_finish<T, N1, N2>(c, t, va);
+    zfast_inv1_finish<T, N1, N2>(c, t + nthr, vb);
   }
 }
 
