@@ -81,14 +81,14 @@ void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
 template <typename T, int SIGN, int N1, int N2, int N3>
 void run_colfast3(const ColArgs<T>& a, int gy, int gz) {
   using S = ColFast3Shape<N1, N2, N3>;
-  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<cplx<LongC<T>>> sm(S::SM_ELEMS);
   const int gx = (a.ncols + S::W - 1) / S::W;
   for (int z = 0; z < gz; ++z)
     for (int y = 0; y < gy; ++y)
       for (int x = 0; x < gx; ++x) {
         const int ncol = std::min(S::W, a.ncols - x * S::W);
         for (int t = 0; t < S::NTHR; ++t) colfast3_twiddles<T, SIGN, S::P>(sm.data(), a.tw, t, S::NTHR);
-        cplx<T>* X = sm.data() + S::P;
+        cplx<LongC<T>>* X = sm.data() + S::P;
         for (int t = 0; t < S::NTHR; ++t)
           colfast3_pass1<T, SIGN, N1, N2, N3, (SIGN > 0)>(a, x, y, z, t, S::NTHR, sm.data(), X);
         for (int t = 0; t < S::NTHR; ++t) colfast3_pass2<T, SIGN, N1, N2, N3>(t, S::NTHR, ncol, sm.data(), X);
@@ -101,13 +101,17 @@ template <typename T, int SIGN, bool CF1, bool CFL>
 void run_col(const ColArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   const bool padded_inverse = SIGN > 0 && a.pad_in && !a.trunc_out && a.nrow_in == 2 * a.h;
   const bool truncated_forward = SIGN < 0 && !a.pad_in && a.trunc_out && a.nrow_out == 2 * a.h;
-  if (g_use_fast && sizeof(T) == 4 && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
+  if (g_use_fast && 3 * a.h == a.pl.n && (padded_inverse || truncated_forward)) {
 #define NS3D_HC_CF3(A, B, C)                              \
     if (a.pl.n == (A) * (B) * (C)) {                      \
       run_colfast3<T, SIGN, A, B, C>(a, L.gy, L.gz);      \
       return;                                             \
     }
-    NS3D_FOR_COLFAST3(NS3D_HC_CF3)
+    if (sizeof(T) == 4) {
+      NS3D_FOR_COLFAST3(NS3D_HC_CF3)
+    } else {        // FP64: the three-pass kernels in double-single arithmetic
+      NS3D_FOR_COLFAST3_F64(NS3D_HC_CF3)
+    }
     if (g_use_fast == 2) {
       NS3D_FOR_LONG_TEST(NS3D_HC_CF3)
     }
@@ -204,13 +208,14 @@ void run_zfast(const ZArgs<T>& a, int nm) {
 template <typename T, int N1, int N2, int N3>
 void run_zfast3(const ZArgs<T>& a, int nm, int nx) {
   using S = ZFast3Shape<N1, N2, N3>;
-  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  using C = LongC<T>;
+  std::vector<cplx<C>> sm(S::SM_ELEMS);
   std::vector<T> red(S::NTHR);
   std::vector<ZFast3State<T, N1, N2, N3>> st(S::NTHR);
   for (int t = 0; t < S::NTHR; ++t) zfast3_twiddles<T, N1, N2, N3>(a, sm.data(), t, S::NTHR);
   for (auto& x : st) {
-    x.umax = T(0);
-    x.chk = T(0);
+    x.umax = C(0);
+    x.chk = C(0);
   }
   int cur = -1;
   auto flush = [&]() {
@@ -247,16 +252,21 @@ void run_zfast3(const ZArgs<T>& a, int nm, int nx) {
 
 template <typename T>
 bool run_z_fast_if_any(const ZArgs<T>& a, int P) {
-  if (sizeof(T) != 4 || 3 * a.h != P) return false;
+  if (3 * a.h != P) return false;
 #define NS3D_HC_ZF3(A, B, C)           \
   if (P == (A) * (B) * (C)) {          \
     run_zfast3<T, A, B, C>(a, 1, P);   \
     return true;                       \
   }
-  NS3D_FOR_ZFAST3(NS3D_HC_ZF3)
+  if (sizeof(T) == 4) {
+    NS3D_FOR_ZFAST3(NS3D_HC_ZF3)
+  } else {          // FP64: the three-pass kernels in double-single arithmetic
+    NS3D_FOR_ZFAST3_F64(NS3D_HC_ZF3)
+  }
   if (g_use_fast == 2) {
     NS3D_FOR_LONG_TEST(NS3D_HC_ZF3)
   }
+  if (sizeof(T) != 4) return false;
 #undef NS3D_HC_ZF3
 #define NS3D_HC_ZF(A, B)               \
   if (P == (A) * (B)) {                \

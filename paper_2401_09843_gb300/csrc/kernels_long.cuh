@@ -11,9 +11,10 @@ namespace ns3d {
 template <typename T, int SIGN, int N1, int N2, int N3>
 __global__ void __launch_bounds__(ColFast3Shape<N1, N2, N3>::NTHR) k_colfast3(ColArgs<T> a) {
   using S = ColFast3Shape<N1, N2, N3>;
+  static_assert(sizeof(cplx<LongC<T>>) == sizeof(cplx<T>), "arithmetic and storage types of one size");
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
-  cplx<T>* tw = reinterpret_cast<cplx<T>*>(ns3d_smem);
-  cplx<T>* X = tw + S::P;
+  cplx<LongC<T>>* tw = reinterpret_cast<cplx<LongC<T>>*>(ns3d_smem);
+  cplx<LongC<T>>* X = tw + S::P;
   const int tid = threadIdx.x;
   colfast3_twiddles<T, SIGN, S::P>(tw, a.tw, tid, S::NTHR);
   __syncthreads();
@@ -41,14 +42,16 @@ __global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR,
                                   sizeof(T) == 8 ? (ZFast3Shape<N1, N2, N3>::NTHR >= 128 ? 2 : 4) : 3)
     k_zfast3(ZArgs<T> a, long long ntiles) {
   using S = ZFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
+  static_assert(sizeof(cplx<C>) == sizeof(cplx<T>), "arithmetic and storage types of one size");
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
-  cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  cplx<C>* sm = reinterpret_cast<cplx<C>*>(ns3d_smem);
   T* red = reinterpret_cast<T*>(sm + S::SM_ELEMS);
   const int tid = threadIdx.x;
   zfast3_twiddles<T, N1, N2, N3>(a, sm, tid, S::NTHR);
   ZFast3State<T, N1, N2, N3> st;
-  st.umax = T(0);
-  st.chk = T(0);
+  st.umax = C(0);
+  st.chk = C(0);
   int cur = -1;
   __syncthreads();
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -61,8 +64,8 @@ __global__ void __launch_bounds__(ZFast3Shape<N1, N2, N3>::NTHR,
         if (tid < 32) zfast3_flush<T>(a, cur, red, S::NTHR, tid);
         __syncthreads();
       }
-      st.umax = T(0);
-      st.chk = T(0);
+      st.umax = C(0);
+      st.chk = C(0);
       cur = bz;
     }
     const ZFast3Ctx<T, N1, N2, N3> c = zfast3_ctx<T, N1, N2, N3>(a, bz, by, y0, sm);

@@ -20,10 +20,13 @@
 //           truncated band known at compile time are not stored)
 //
 // One shared line of P + 1 elements per column (odd stride: the 16 columns a
-// warp touches fall in distinct banks).
+// warp touches fall in distinct banks).  Storage type T (global memory),
+// arithmetic type C = LongC<T> (registers and shared memory): FP64 data are
+// transformed in double-single arithmetic (ns3d_df64.cuh).
 #pragma once
 
 #include "ns3d_blocks.cuh"
+#include "ns3d_df64.cuh"
 
 // Long transform lengths with a three-pass register column pass (FP32),
 // used with the default padding h = N/2 = P/3.
@@ -40,19 +43,20 @@ struct ColFast3Shape {
 };
 
 template <typename T, int SIGN, int P>
-NS3D_HD void colfast3_twiddles(cplx<T>* tw, const cplx<T>* gtw, int tid, int nthr) {
+NS3D_HD void colfast3_twiddles(cplx<LongC<T>>* tw, const cplx<T>* gtw, int tid, int nthr) {
   for (int e = tid; e < P; e += nthr) {
     cplx<T> w = gtw[e];
     if (SIGN > 0) w.y = -w.y;
-    tw[e] = w;
+    tw[e] = ccvt<LongC<T>>(w);
   }
 }
 
 // PAD: the input has N = 2H rows spread over the P positions (inverse).
 template <typename T, int SIGN, int N1, int N2, int N3, bool PAD>
 NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
-                            const cplx<T>* tw, cplx<T>* X) {
+                            const cplx<LongC<T>>* tw, cplx<LongC<T>>* X) {
   using S = ColFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
   constexpr int M = N2 * N3;
   const int c0 = bx * S::W;
   const int ncol = imin(S::W, a.ncols - c0);
@@ -64,44 +68,46 @@ NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid
     if (col >= ncol) continue;
     const cplx<T>* ic = in + col * a.in_cs;
     const int rs = (int)a.in_rs;   // P rs < 2^31 (checked at dispatch)
-    cplx<T> v[N1];
+    cplx<C> v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       const int p = M * j1 + jp;
       if (!PAD) {
-        v[j1] = ic[p * rs];
+        v[j1] = ccvt<C>(ic[p * rs]);
       } else {
         const int reg = pad_region(M * j1, M, S::P, S::H);
         if (reg == PAD_ZERO) {
-          v[j1] = czero<T>();
+          v[j1] = czero<C>();
         } else if (reg == PAD_LOW) {
-          v[j1] = ic[p * rs];
+          v[j1] = ccvt<C>(ic[p * rs]);
         } else if (reg == PAD_HIGH) {
-          v[j1] = ic[(p - S::H) * rs];          // row p - P + N
+          v[j1] = ccvt<C>(ic[(p - S::H) * rs]);   // row p - P + N
         } else {
           const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
-          v[j1] = row >= 0 ? ic[row * rs] : czero<T>();
+          v[j1] = row >= 0 ? ccvt<C>(ic[row * rs]) : czero<C>();
         }
       }
     }
     Dft<N1, SIGN>::run(v);
-    cplx<T>* D = X + col * S::LP + jp * N1;
+    cplx<C>* D = X + col * S::LP + jp * N1;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) D[k1] = k1 == 0 ? v[k1] : v[k1] * tw[jp * k1];   // tw[0] = 1
   }
 }
 
 template <typename T, int SIGN, int N1, int N2, int N3>
-NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<T>* tw, cplx<T>* X) {
+NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<LongC<T>>* tw,
+                            cplx<LongC<T>>* X) {
   using S = ColFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
 #pragma unroll 1
   for (int t = tid; t < S::W * N1 * N3; t += nthr) {
     const int col = t % S::W;
     const int r = t / S::W;
     const int k1 = r % N1, j3 = r / N1;
     if (col >= ncol) continue;
-    cplx<T>* D = X + col * S::LP + j3 * N1 + k1;
-    cplx<T> v[N2];
+    cplx<C>* D = X + col * S::LP + j3 * N1 + k1;
+    cplx<C> v[N2];
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) v[j2] = D[j2 * N3 * N1];
     Dft<N2, SIGN>::run(v);
@@ -113,8 +119,10 @@ NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<T>* tw, cplx
 // TRUNC: only the N = 2H retained positions are stored (forward).
 template <typename T, int SIGN, int N1, int N2, int N3, bool TRUNC>
 NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
-                            const cplx<T>* X) {
+                            const cplx<LongC<T>>* X) {
   using S = ColFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
+  const C scale = (C)a.scale;
   constexpr int M = N1 * N2;
   const int c0 = bx * S::W;
   const int ncol = imin(S::W, a.ncols - c0);
@@ -125,8 +133,8 @@ NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid
     const int r = t / S::W;
     const int k1 = r % N1, k2 = r / N1;
     if (col >= ncol) continue;
-    const cplx<T>* D = X + col * S::LP + k2 * N3 * N1 + k1;
-    cplx<T> v[N3];
+    const cplx<C>* D = X + col * S::LP + k2 * N3 * N1 + k1;
+    cplx<C> v[N3];
 #pragma unroll
     for (int j3 = 0; j3 < N3; ++j3) v[j3] = D[j3 * N1];
     Dft<N3, SIGN>::run(v);
@@ -136,16 +144,16 @@ NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid
     for (int k3 = 0; k3 < N3; ++k3) {
       const int p = r + M * k3;
       if (!TRUNC) {
-        oc[p * rs] = a.scale * v[k3];
+        oc[p * rs] = ccvt<T>(scale * v[k3]);
       } else {
         const int reg = pad_region(M * k3, M, S::P, S::H);
         if (reg == PAD_LOW) {
-          oc[p * rs] = a.scale * v[k3];
+          oc[p * rs] = ccvt<T>(scale * v[k3]);
         } else if (reg == PAD_HIGH) {
-          oc[(p - S::H) * rs] = a.scale * v[k3];
+          oc[(p - S::H) * rs] = ccvt<T>(scale * v[k3]);
         } else if (reg == PAD_MIXED) {
           const int row = pad_row_of(p, S::P, S::H, 2 * S::H);
-          if (row >= 0) oc[row * rs] = a.scale * v[k3];
+          if (row >= 0) oc[row * rs] = ccvt<T>(scale * v[k3]);
         }
       }
     }

@@ -27,10 +27,15 @@
 // either consecutive a across lanes or rows of odd stride, so no two lanes of
 // a half-warp share a bank.  Blocks are persistent over the (member, x, pair)
 // tiles so that the twiddle tables are loaded once per block; the CFL maximum
-// is accumulated per thread and reduced when the member changes.
+// is accumulated per thread and reduced when the member changes.  Storage type
+// T (global memory), arithmetic type C = LongC<T> (registers, shared memory):
+// FP64 data are transformed in double-single arithmetic (ns3d_df64.cuh).
 #pragma once
 
 #include "ns3d_blocks.cuh"
+#include "ns3d_df64.cuh"
+
+template <> NS3D_HD df64 big_finite<df64>() { return df64(3.4028234663852886e38f); }
 
 #define NS3D_FOR_ZFAST3(X) X(16, 12, 8)
 // FP64 (FP64-ALU-bound: the compile-time pruning of the padding and
@@ -56,21 +61,23 @@ struct ZFast3Shape {
 
 template <typename T, int N1, int N2, int N3>
 struct ZFast3State {
-  cplx<T> z[3][N3];   // inverse results at positions k1 + N1 k2 + N1 N2 k3
-  T umax;             // running max of |u0| + |u1| + |u2| (current member)
-  T chk;              // 0 while every point seen is finite
+  using C = LongC<T>;
+  cplx<C> z[3][N3];   // inverse results at positions k1 + N1 k2 + N1 N2 k3
+  C umax;             // running max of |u0| + |u1| + |u2| (current member)
+  C chk;              // 0 while every point seen is finite
 };
 
 template <typename T, int N1, int N2, int N3>
 struct ZFast3Ctx {
+  using C = LongC<T>;
   const ZArgs<T>* a;
   const cplx<T>* in;   // the pair's first column: [comp][col][kz], col stride h
   cplx<T>* out;
-  const cplx<T>* T1;
-  const cplx<T>* T3;
-  const cplx<T>* wf;   // w_M^e = w_P^(N1 e)
-  const cplx<T>* wi;   // conjugate
-  cplx<T>* X;
+  const cplx<C>* T1;
+  const cplx<C>* T3;
+  const cplx<C>* wf;   // w_M^e = w_P^(N1 e)
+  const cplx<C>* wi;   // conjugate
+  cplx<C>* X;
 };
 
 // tile t of a launch: member, x row, pair of y columns
@@ -86,7 +93,7 @@ NS3D_HD void zfast3_tile(long long t, int* bz, int* by, int* y0) {
 
 template <typename T, int N1, int N2, int N3>
 NS3D_HD ZFast3Ctx<T, N1, N2, N3> zfast3_ctx(const ZArgs<T>& a, int bz, int by, int y0,
-                                            cplx<T>* sm) {
+                                            cplx<LongC<T>>* sm) {
   using S = ZFast3Shape<N1, N2, N3>;
   ZFast3Ctx<T, N1, N2, N3> c;
   c.a = &a;
@@ -101,19 +108,20 @@ NS3D_HD ZFast3Ctx<T, N1, N2, N3> zfast3_ctx(const ZArgs<T>& a, int bz, int by, i
 }
 
 template <typename T, int N1, int N2, int N3>
-NS3D_HD void zfast3_twiddles(const ZArgs<T>& a, cplx<T>* sm, int tid, int nthr) {
+NS3D_HD void zfast3_twiddles(const ZArgs<T>& a, cplx<LongC<T>>* sm, int tid, int nthr) {
   using S = ZFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
   for (int e = tid; e < S::P; e += nthr) {
     const int k1 = e / S::M, jp = e % S::M;       // T1[k1][j'] = conj w^(j' k1)
     const cplx<T> w1 = a.tw[jp * k1];
-    sm[e] = cmake(w1.x, -w1.y);
+    sm[e] = ccvt<C>(cmake(w1.x, -w1.y));
     const int i = e / N1, aa = e % N1;            // T3[i][a] = w^(a i)
-    sm[S::OFF_T3 + e] = a.tw[aa * i];
+    sm[S::OFF_T3 + e] = ccvt<C>(a.tw[aa * i]);
   }
   for (int e = tid; e < S::M; e += nthr) {
     const cplx<T> w = a.tw[N1 * e];
-    sm[S::OFF_WM + e] = w;
-    sm[S::OFF_WM + S::M + e] = cmake(w.x, -w.y);
+    sm[S::OFF_WM + e] = ccvt<C>(w);
+    sm[S::OFF_WM + S::M + e] = ccvt<C>(cmake(w.x, -w.y));
   }
 }
 
@@ -121,6 +129,7 @@ NS3D_HD void zfast3_twiddles(const ZArgs<T>& a, cplx<T>* sm, int tid, int nthr) 
 template <typename T, int N1, int N2, int N3>
 NS3D_HD void zfast3_inv1(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr) {
   using S = ZFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
   constexpr int h = S::H, M = S::M;
   const ZArgs<T>& a = *c.a;
   for (int t = tid; t < 3 * M; t += nthr) {
@@ -129,30 +138,30 @@ NS3D_HD void zfast3_inv1(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr) {
     const int ca = l == 1 ? 1 : 0, cb = l == 0 ? 0 : 1;
     const cplx<T>* ia = c.in + (l == 2 ? 2 : 0) * a.in_cs + ca * h;
     const cplx<T>* ib = c.in + (l == 2 ? 2 : 1) * a.in_cs + cb * h;
-    cplx<T> v[N1];
+    cplx<C> v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
       const int p = M * j1 + jp;
       const int reg = pad_region(M * j1, M, S::P, S::H);
       if (reg == PAD_ZERO) {
-        v[j1] = czero<T>();
+        v[j1] = czero<C>();
       } else if (reg == PAD_LOW) {               // u_a[p] + i u_b[p]
-        cplx<T> x = ia[p], y = ib[p];
+        cplx<C> x = ccvt<C>(ia[p]), y = ccvt<C>(ib[p]);
         if (j1 == 0 && jp == 0) {                // a real line has a real mean
-          x.y = T(0);
-          y.y = T(0);
+          x.y = C(0);
+          y.y = C(0);
         }
         v[j1] = cmake(x.x - y.y, x.y + y.x);
       } else if (reg == PAD_HIGH) {              // conj(u_a[P-p]) + i conj(u_b[P-p])
-        const cplx<T> x = ia[S::P - p], y = ib[S::P - p];
+        const cplx<C> x = ccvt<C>(ia[S::P - p]), y = ccvt<C>(ib[S::P - p]);
         v[j1] = cmake(x.x + y.y, -x.y + y.x);
       } else {
-        v[j1] = pack2(ia, ib, S::P, S::H, p, 0, 0, 1);
+        v[j1] = ccvt<C>(pack2(ia, ib, S::P, S::H, p, 0, 0, 1));
       }
     }
     Dft<N1, +1>::run(v);
-    cplx<T>* D = c.X + l * S::LP + jp * S::LR;
-    const cplx<T>* tw = c.T1 + jp;
+    cplx<C>* D = c.X + l * S::LP + jp * S::LR;
+    const cplx<C>* tw = c.T1 + jp;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) D[k1] = k1 == 0 ? v[k1] : v[k1] * tw[k1 * M];
   }
@@ -164,8 +173,8 @@ NS3D_HD void zfast3_inv2(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr) {
   using S = ZFast3Shape<N1, N2, N3>;
   for (int t = tid; t < 3 * N1 * N3; t += nthr) {
     const int k1 = t % N1, j3 = (t / N1) % N3, l = t / (N1 * N3);
-    cplx<T>* D = c.X + l * S::LP + j3 * S::LR + k1;
-    cplx<T> v[N2];
+    cplx<LongC<T>>* D = c.X + l * S::LP + j3 * S::LR + k1;
+    cplx<LongC<T>> v[N2];
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) v[j2] = D[j2 * N3 * S::LR];
     Dft<N2, +1>::run(v);
@@ -179,10 +188,11 @@ template <typename T, int N1, int N2, int N3>
 NS3D_HD void zfast3_inv3(const ZFast3Ctx<T, N1, N2, N3>& c, int tid,
                          ZFast3State<T, N1, N2, N3>& st) {
   using S = ZFast3Shape<N1, N2, N3>;
+  using C = LongC<T>;
   const int k1 = tid % N1, k2 = tid / N1;
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
-    const cplx<T>* D = c.X + l * S::LP + k2 * N3 * S::LR + k1;
+    const cplx<C>* D = c.X + l * S::LP + k2 * N3 * S::LR + k1;
 #pragma unroll
     for (int j3 = 0; j3 < N3; ++j3) st.z[l][j3] = D[j3 * S::LR];
     Dft<N3, +1>::run(st.z[l]);
@@ -190,20 +200,21 @@ NS3D_HD void zfast3_inv3(const ZFast3Ctx<T, N1, N2, N3>& c, int tid,
   // 0 * s is NaN exactly when s is not finite
 #pragma unroll
   for (int k3 = 0; k3 < N3; ++k3) {
-    const T sa = xabs(st.z[0][k3].x) + xabs(st.z[0][k3].y) + xabs(st.z[2][k3].x);
-    const T sb = xabs(st.z[1][k3].x) + xabs(st.z[1][k3].y) + xabs(st.z[2][k3].y);
+    const C sa = xabs(st.z[0][k3].x) + xabs(st.z[0][k3].y) + xabs(st.z[2][k3].x);
+    const C sb = xabs(st.z[1][k3].x) + xabs(st.z[1][k3].y) + xabs(st.z[2][k3].y);
     st.umax = xmax(st.umax, xmax(sa, sb));
-    st.chk = st.chk + T(0) * sa + T(0) * sb;
+    st.chk = st.chk + C(0) * sa + C(0) * sb;
   }
 }
 
 // product line f (0..5) at register position k3: column f % 2, products
 // (00, 01), (02, 11), (12, 22) for f / 2 = 0, 1, 2
 template <typename T, int N1, int N2, int N3>
-NS3D_HD cplx<T> zfast3_product(const ZFast3State<T, N1, N2, N3>& st, int f, int k3) {
+NS3D_HD cplx<LongC<T>> zfast3_product(const ZFast3State<T, N1, N2, N3>& st, int f, int k3) {
+  using C = LongC<T>;
   const int col = f & 1;
-  const T u0 = st.z[col][k3].x, u1 = st.z[col][k3].y;
-  const T u2 = col ? st.z[2][k3].y : st.z[2][k3].x;
+  const C u0 = st.z[col][k3].x, u1 = st.z[col][k3].y;
+  const C u2 = col ? st.z[2][k3].y : st.z[2][k3].x;
   const int pr = f >> 1;
   if (pr == 0) return cmake(u0 * u0, u0 * u1);
   if (pr == 1) return cmake(u0 * u2, u1 * u1);
@@ -218,11 +229,11 @@ NS3D_HD void zfast3_fwdA(const ZFast3Ctx<T, N1, N2, N3>& c, int tid,
   const int a = tid % N1, b = tid / N1;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    cplx<T> v[N3];
+    cplx<LongC<T>> v[N3];
 #pragma unroll
     for (int k3 = 0; k3 < N3; ++k3) v[k3] = zfast3_product<T, N1, N2, N3>(st, 3 * r + q, k3);
     Dft<N3, -1>::run(v);
-    cplx<T>* D = c.X + q * S::LP + N3 * b * S::LR + a;
+    cplx<LongC<T>>* D = c.X + q * S::LP + N3 * b * S::LR + a;
 #pragma unroll
     for (int f3 = 0; f3 < N3; ++f3) D[f3 * S::LR] = f3 == 0 ? v[f3] : v[f3] * c.wf[b * f3];
   }
@@ -234,12 +245,12 @@ NS3D_HD void zfast3_fwdB(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr) {
   using S = ZFast3Shape<N1, N2, N3>;
   for (int t = tid; t < 3 * N1 * N3; t += nthr) {
     const int a = t % N1, f3 = (t / N1) % N3, q = t / (N1 * N3);
-    cplx<T>* D = c.X + q * S::LP + f3 * S::LR + a;
-    cplx<T> v[N2];
+    cplx<LongC<T>>* D = c.X + q * S::LP + f3 * S::LR + a;
+    cplx<LongC<T>> v[N2];
 #pragma unroll
     for (int b = 0; b < N2; ++b) v[b] = D[b * N3 * S::LR];
     Dft<N2, -1>::run(v);
-    const cplx<T>* tw = c.T3 + f3 * N1 + a;      // T3[f3 + N3 f2][a]
+    const cplx<LongC<T>>* tw = c.T3 + f3 * N1 + a;      // T3[f3 + N3 f2][a]
 #pragma unroll
     for (int f2 = 0; f2 < N2; ++f2) D[f2 * N3 * S::LR] = v[f2] * tw[f2 * N3 * N1];
   }
@@ -251,8 +262,8 @@ NS3D_HD void zfast3_fwdC(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr) {
   using S = ZFast3Shape<N1, N2, N3>;
   for (int t = tid; t < 3 * S::M; t += nthr) {
     const int i = t % S::M, q = t / S::M;
-    cplx<T>* D = c.X + q * S::LP + i * S::LR;
-    cplx<T> v[N1];
+    cplx<LongC<T>>* D = c.X + q * S::LP + i * S::LR;
+    cplx<LongC<T>> v[N1];
 #pragma unroll
     for (int aa = 0; aa < N1; ++aa) v[aa] = D[aa];
     Dft<N1, -1>::run(v);
@@ -279,12 +290,13 @@ NS3D_HD void zfast3_extract(const ZFast3Ctx<T, N1, N2, N3>& c, int tid, int nthr
     const int k = t % h, q = t / h;
     const int f = 3 * r + q;
     const int col = f & 1, comp = 2 * (f >> 1);
-    const cplx<T>* X = c.X + q * S::LP;
-    const cplx<T> zk = X[zfast3_fpos<N1, N2, N3>(k)];
-    const cplx<T> zm = cconj(X[zfast3_fpos<N1, N2, N3>(k == 0 ? 0 : S::P - k)]);
-    const cplx<T> s = zk + zm, d = zk - zm;
-    c.out[comp * a.out_cs + col * h + k] = cmake(T(0.5) * s.x, T(0.5) * s.y);
-    c.out[(comp + 1) * a.out_cs + col * h + k] = cmake(T(0.5) * d.y, T(-0.5) * d.x);
+    using C = LongC<T>;
+    const cplx<C>* X = c.X + q * S::LP;
+    const cplx<C> zk = X[zfast3_fpos<N1, N2, N3>(k)];
+    const cplx<C> zm = cconj(X[zfast3_fpos<N1, N2, N3>(k == 0 ? 0 : S::P - k)]);
+    const cplx<C> s = zk + zm, d = zk - zm;
+    c.out[comp * a.out_cs + col * h + k] = ccvt<T>(cmake(C(0.5) * s.x, C(0.5) * s.y));
+    c.out[(comp + 1) * a.out_cs + col * h + k] = ccvt<T>(cmake(C(0.5) * d.y, C(-0.5) * d.x));
   }
 }
 
@@ -322,5 +334,6 @@ NS3D_HD void zfast3_flush(const ZArgs<T>& a, int bz, const T* red, int nthr, int
 
 template <typename T, int N1, int N2, int N3>
 NS3D_HD T zfast3_red_value(const ZFast3State<T, N1, N2, N3>& st) {
-  return (!(st.chk == T(0)) || !(st.umax <= big_finite<T>())) ? T(-1) : st.umax;
+  using C = LongC<T>;
+  return (!(st.chk == C(0)) || !(st.umax <= big_finite<C>())) ? T(-1) : (T)st.umax;
 }

@@ -314,6 +314,30 @@ def test_emulated_three_pass_kernels_match_oracle(built, N):
         lib.ns3d_hostcheck_use_fast(1)
 
 
+@pytest.mark.parametrize("N", [32, 64])
+def test_emulated_three_pass_kernels_fp64_double_single(built, N):
+    """FP64 plans run their three-pass column and z kernels in double-single
+    arithmetic (two FP32 per value, 48-bit significand): emulated at P = 48 =
+    4x3x4 and 96 = 6x4x4 thread by thread, the RHS of a sparse field against
+    the Galerkin product and two fixed steps against the oracle, both within
+    the FP64 tolerance 1e-11 (the arithmetic's unit roundoff is 2^-48)."""
+    prm = S.Params(nu=0.01, eps0=1.0)
+    uh = I.sparse_random(N, seed=N + 11, nmodes=24)
+    ref = S.rhs_by_convolution(uh, prm)
+    lib = ctypes.CDLL(built.HOSTLIB)
+    lib.ns3d_hostcheck_use_fast(2)
+    try:
+        got, rc, _ = hostcheck(built, uh, 3 * N // 2, prm, dtype=1)
+        assert rc == 0 and rel(got, ref) < 1e-12, rel(got, ref)
+        u0 = I.random_spectrum(N, seed=N + 1, k0=3.0)
+        sref, _, _ = S.integrate(u0, prm.with_(dt_fixed=0.01), 2)
+        got, rc, t = hostcheck(built, u0, 3 * N // 2, prm, nsteps=2, dt=0.01, dtype=1)
+        assert rc == 0 and abs(t - 0.02) < 1e-15
+        assert rel(got, sref) < 1e-12, rel(got, sref)
+    finally:
+        lib.ns3d_hostcheck_use_fast(1)
+
+
 @pytest.mark.parametrize("sign", [1, -1])
 def test_three_pass_column_block_1536(built, sign):
     """One column pass of the P = 1536 = 16x12x8 kernel (N = 1024), emulated:
