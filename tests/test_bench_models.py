@@ -82,3 +82,16 @@ def test_traffic_entry_names_its_capture():
     if src is not None:
         assert os.path.exists(os.path.join(ROOT, src))
     assert bench.traffic_entry("zpass", 999, "f32", 1) == (None, None)
+
+
+def test_fp64_roofline_model():
+    """FP64 lines: the flop model times the double-single cost per flop (a sum
+    11 FP32 operations, a product 7, two sums per product) against the FP32
+    pipe (152 SMs x 128 lanes x 2.07 GHz)."""
+    assert abs(bench.FP32_OPS_PEAK_T - 40.27392) < 1e-9
+    assert abs(bench.DF64_OPS_PER_FLOP - 29.0 / 3.0) < 1e-15
+    r = bench.fp64_roofline(256, 384, 60.0)
+    f = bench.fft_flops_per_step(256, 384)
+    assert abs(r["achieved"] - f * 29 / 3 / 0.06 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 40.27392) < 1e-15
+    assert abs(r["fp64_equivalent_TFLOPs"] - f / 0.06 / 1e12) < 1e-12
