@@ -69,7 +69,9 @@ typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
  *   (|k| the integer wavenumber; the paper's "+eps_N" is read as damping).
  *   n_pad: padded FFT size P.  0: chosen at plan creation (section 3.1): the
  *          smallest 2^a 3^b 5^c 7^d >= 3N/2 where the register kernels exist
- *          (FP32, P = 3N/2 in {48, 96, 192, 384, 1536}), otherwise the fastest
+ *          (FP32, P = 3N/2 in {48, 96, 192, 384, 1536}; FP64, P = 3N/2 in
+ *          {192, 384, 1152}, transformed in double-single arithmetic with a
+ *          48-bit significand, binary64 in memory), otherwise the fastest
  *          of the 7-smooth sizes up to 12.5% above it by a timed right-hand
  *          side (cached per device, N and dtype; also in the file named by the
  *          environment variable NS3D_AUTOTUNE_CACHE, if set).  -1: the

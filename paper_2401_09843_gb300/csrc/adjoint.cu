@@ -7,8 +7,9 @@
 //   lam_n = 1/3 lam + 3/4 a2 + a1 + dt J(u)^T a1,
 // J(u)^T w = T_N F[sum_l u_l S_jl(Leray w)] - lambda w (ns3d_blocks.cuh).
 // One evaluation of J^T: spectral prep (S from w), inverse x and y of 9
-// components (u and S), the adjoint z pass (products), forward y and x of 3
-// components, and the combine.  dt is the plan's fixed step.
+// components (u and S), the adjoint z pass (products; register-resident in
+// FP32 at the forward register kernel's sizes, ns3d_zadj.cuh), forward y and
+// x of 3 components, and the combine.  dt is the plan's fixed step.
 #include <vector>
 
 #include "ns3d.h"
@@ -214,21 +215,40 @@ ns3d_status adjoint_products(AdjWork<T>& W, const cplx<T>* u, const cplx<T>* w, 
   Launch ly = launch_inv_y(g, 1);
   ly.gz = 9;
   NS3D_CUDA(launch_col<T>(ay, COL_INV_CC, ly, s));
-  ZAdjArgs<T> az{};
-  az.in = W.B9;
-  az.out = W.A9;
-  az.tw = W.tw;
-  az.pl = g.plP;
-  az.P = P;
-  az.h = h;
-  int Wz = 8;
-  while (Wz > 2 && (size_t)7 * P * (Wz + 1) * sizeof(cplx<T>) > 200 * 1024) Wz /= 2;
-  az.W = Wz;
-  az.ldw = Wz + 1;
-  const size_t smz = (size_t)7 * P * az.ldw * sizeof(cplx<T>);
-  NS3D_CUDA(cudaFuncSetAttribute((const void*)k_zadj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-  k_zadj<T><<<dim3(cdiv(P, Wz), P), 128, smz, s>>>(az);
-  NS3D_CUDA(cudaGetLastError());
+  if (sizeof(T) == 4 && 3 * h == P && zfast_available<float>(P)) {
+    // register-resident adjoint z pass (ns3d_zadj.cuh)
+    ZArgs<float> za{};
+    za.in = reinterpret_cast<const cplx<float>*>(W.B9);
+    za.out = reinterpret_cast<cplx<float>*>(W.A9);
+    za.tw = reinterpret_cast<const cplx<float>*>(W.tw);
+    za.P = P;
+    za.h = h;
+    za.in_cs = za.out_cs = (long long)P * P * h;
+    za.xs = (long long)P * h;
+    za.ctrl = nullptr;
+    cudaError_t e = cudaErrorInvalidValue;
+#define NS3D_ZADJ_GO(A, B) \
+    if (P == (A) * (B)) e = zadjf_launch<float, A, B>(za, 1, s);
+    NS3D_FOR_ZFAST(NS3D_ZADJ_GO)
+#undef NS3D_ZADJ_GO
+    NS3D_CUDA(e);
+  } else {
+    ZAdjArgs<T> az{};
+    az.in = W.B9;
+    az.out = W.A9;
+    az.tw = W.tw;
+    az.pl = g.plP;
+    az.P = P;
+    az.h = h;
+    int Wz = 8;
+    while (Wz > 2 && (size_t)7 * P * (Wz + 1) * sizeof(cplx<T>) > 200 * 1024) Wz /= 2;
+    az.W = Wz;
+    az.ldw = Wz + 1;
+    const size_t smz = (size_t)7 * P * az.ldw * sizeof(cplx<T>);
+    NS3D_CUDA(cudaFuncSetAttribute((const void*)k_zadj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    k_zadj<T><<<dim3(cdiv(P, Wz), P), 128, smz, s>>>(az);
+    NS3D_CUDA(cudaGetLastError());
+  }
   ColArgs<T> fy = args_fwd_y<T>(g, W.A9, W.B9, W.tw);
   Launch lfy = launch_fwd_y(g, 1);
   lfy.gz = 3;

@@ -16,6 +16,7 @@
 #include "ns3d_colfast3.cuh"
 #include "ns3d_zfast3.cuh"
 #include "ns3d_zrot.cuh"
+#include "ns3d_zadj.cuh"
 
 namespace {
 
@@ -80,7 +81,7 @@ void run_colfast(const ColArgs<T>& a, const ns3d::Launch& L) {
 
 template <typename T, int SIGN, int N1, int N2, int N3>
 void run_colfast3(const ColArgs<T>& a, int gy, int gz) {
-  using S = ColFast3Shape<N1, N2, N3>;
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   std::vector<cplx<LongC<T>>> sm(S::SM_ELEMS);
   const int gx = (a.ncols + S::W - 1) / S::W;
   for (int z = 0; z < gz; ++z)
@@ -139,6 +140,26 @@ void run_z(const ZArgs<T>& a, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   for (int z = 0; z < L.gz; ++z)
     for (int y = 0; y < L.gy; ++y)
       for (int x = 0; x < L.gx; ++x) zfused_block<T>(a, x, y, z, 0, 1, sm.data(), red, HostSync{});
+}
+
+// The adjoint right-hand side's register-resident z pass, phase by phase and
+// thread by thread, on x rows by < nx.
+template <typename T, int N1, int N2>
+void run_zadjf(const ZArgs<T>& a, int nx) {
+  using S = ZAdjShape<N1, N2>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<ZAdjState<T, N1, N2>> st(S::NTHR);
+  const int gx = (S::P + S::Y - 1) / S::Y;
+  for (int by = 0; by < nx; ++by)
+    for (int bx = 0; bx < gx; ++bx) {
+      ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2>(a, bx, by, 0, sm.data());
+      for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
+      for (int t = 0; t < S::NTHR; ++t) zadjf_inv1(c, t, S::NTHR);
+      for (int t = 0; t < S::NTHR; ++t) zadjf_inv2(c, t, st[t]);
+      for (int t = 0; t < S::NTHR; ++t) zadjf_fwd1(c, t, st[t]);
+      for (int t = 0; t < S::NTHR; ++t) zadjf_fwd2(c, t, S::NTHR);
+      for (int t = 0; t < S::NTHR; ++t) zadjf_extract(c, t, S::NTHR);
+    }
 }
 
 // The rotational form's register-resident z pass, phase by phase and thread
@@ -617,6 +638,45 @@ int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
   run_zfast3<float, 16, 12, 8>(a, 1, nx);
   std::memcpy(umax, &ctrl.umax_bits, sizeof(double));
   return ctrl.status;
+}
+
+// The adjoint z pass on x rows < nx of a [9][P][P][h] complex64 array: the
+// register-resident kernel into out_fast and the generic tile block into
+// out_generic (both [3][P][P][h]).  P must be a register size (48, 96, 192,
+// 384); returns -1 otherwise.
+int ns3d_hostcheck_zadj(int P, const void* in, void* out_fast, void* out_generic, int nx) {
+  const int h = P / 3;
+  const std::vector<cplx<float>> tw = ns3d::make_twiddles<float>(P);
+  ZArgs<float> a{};
+  a.in = static_cast<const cplx<float>*>(in);
+  a.out = static_cast<cplx<float>*>(out_fast);
+  a.tw = tw.data();
+  a.P = P;
+  a.h = h;
+  a.in_cs = a.out_cs = (long long)P * P * h;
+  a.xs = (long long)P * h;
+  bool done = false;
+#define NS3D_HC_ZA(A, B)              \
+  if (P == (A) * (B)) {               \
+    run_zadjf<float, A, B>(a, nx);    \
+    done = true;                      \
+  }
+  NS3D_FOR_ZFAST(NS3D_HC_ZA)
+#undef NS3D_HC_ZA
+  if (!done) return -1;
+  ZAdjArgs<float> g{};
+  g.in = static_cast<const cplx<float>*>(in);
+  g.out = static_cast<cplx<float>*>(out_generic);
+  g.tw = tw.data();
+  if (!ns3d::make_fft_plan(P, &g.pl)) return -1;
+  g.P = P;
+  g.h = h;
+  g.W = 8;
+  g.ldw = 9;
+  std::vector<cplx<float>> sm((size_t)7 * P * g.ldw);
+  for (int by = 0; by < nx; ++by)
+    for (int bx = 0; bx < (P + g.W - 1) / g.W; ++bx) zadj_block<float>(g, bx, by, 0, 1, sm.data(), HostSync{});
+  return 0;
 }
 
 // Radix plan chosen for length n (for tests).

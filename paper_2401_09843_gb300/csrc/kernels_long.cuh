@@ -9,8 +9,8 @@
 namespace ns3d {
 
 template <typename T, int SIGN, int N1, int N2, int N3>
-__global__ void __launch_bounds__(ColFast3Shape<N1, N2, N3>::NTHR) k_colfast3(ColArgs<T> a) {
-  using S = ColFast3Shape<N1, N2, N3>;
+__global__ void __launch_bounds__(ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>::NTHR) k_colfast3(ColArgs<T> a) {
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   static_assert(sizeof(cplx<LongC<T>>) == sizeof(cplx<T>), "arithmetic and storage types of one size");
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<LongC<T>>* tw = reinterpret_cast<cplx<LongC<T>>*>(ns3d_smem);
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(ColFast3Shape<N1, N2, N3>::NTHR) k_colfast3(Co
 
 template <typename T, int SIGN, int N1, int N2, int N3>
 cudaError_t colfast3_launch(const ColArgs<T>& a, const Launch& L, cudaStream_t s) {
-  using S = ColFast3Shape<N1, N2, N3>;
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   const size_t smem = (size_t)S::SM_ELEMS * sizeof(cplx<T>);
   dim3 grid((a.ncols + S::W - 1) / S::W, L.gy, L.gz);
   k_colfast3<T, SIGN, N1, N2, N3><<<grid, S::NTHR, smem, s>>>(a);
@@ -125,7 +125,7 @@ cudaError_t zfast3_init() {
 
 template <typename T, int N1, int N2, int N3>
 cudaError_t long_init() {
-  static_assert(ColFast3Shape<N1, N2, N3>::SM_ELEMS * sizeof(cplx<T>) <= 227 * 1024,
+  static_assert(ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>::SM_ELEMS * sizeof(cplx<T>) <= 227 * 1024,
                 "three-pass column: shared memory");
   const void* f[2] = {(const void*)k_colfast3<T, +1, N1, N2, N3>,
                       (const void*)k_colfast3<T, -1, N1, N2, N3>};

@@ -4,6 +4,7 @@
 #include "kernels_col.cuh"
 #include "ns3d_zfast.cuh"
 #include "ns3d_zrot.cuh"
+#include "ns3d_zadj.cuh"
 
 namespace ns3d {
 
@@ -101,6 +102,47 @@ cudaError_t zrot_init() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
+// The adjoint right-hand side's register-resident z pass (ns3d_zadj.cuh), same sizes.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
+  using S = ZAdjShape<N1, N2>;
+  extern __shared__ __align__(16) unsigned char ns3d_smem[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  const ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+  const int tid = threadIdx.x;
+  zfast_load_twiddles(c, tid, S::NTHR);
+  __syncthreads();
+  zadjf_inv1(c, tid, S::NTHR);
+  __syncthreads();
+  ZAdjState<T, N1, N2> st;
+  zadjf_inv2(c, tid, st);
+  __syncthreads();
+  zadjf_fwd1(c, tid, st);
+  __syncthreads();
+  zadjf_fwd2(c, tid, S::NTHR);
+  __syncthreads();
+  zadjf_extract(c, tid, S::NTHR);
+}
+
+template <typename T, int N1, int N2>
+size_t zadjf_smem() {
+  return (size_t)ZAdjShape<N1, N2>::SM_ELEMS * sizeof(cplx<T>);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zadjf_launch(const ZArgs<T>& a, int nm, cudaStream_t s) {
+  using S = ZAdjShape<N1, N2>;
+  dim3 grid((S::P + S::Y - 1) / S::Y, S::P, nm);
+  k_zadjf<T, N1, N2><<<grid, S::NTHR, zadjf_smem<T, N1, N2>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zadjf_init() {
+  return cudaFuncSetAttribute((const void*)k_zadjf<T, N1, N2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 }  // namespace ns3d
 
 #define NS3D_ZFAST_VARIANT(T, N1, N2)                                                        \
@@ -109,4 +151,6 @@ cudaError_t zrot_init() {
   template cudaError_t zfast_init<T, N1, N2>();                                              \
   template cudaError_t zrot_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);           \
   template cudaError_t zrot_init<T, N1, N2>();                                               \
+  template cudaError_t zadjf_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);          \
+  template cudaError_t zadjf_init<T, N1, N2>();                                              \
   }

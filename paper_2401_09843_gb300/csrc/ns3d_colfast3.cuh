@@ -32,11 +32,13 @@
 // used with the default padding h = N/2 = P/3.
 #define NS3D_FOR_COLFAST3(X) X(16, 12, 8)
 
-template <int N1, int N2, int N3>
+// ESZ: bytes of one complex element (8 FP32, 16 FP64)
+template <int N1, int N2, int N3, int ESZ = 8>
 struct ColFast3Shape {
   static constexpr int P = N1 * N2 * N3;
   static constexpr int H = P / 3;        // N/2 of the default padding P = 3N/2
-  static constexpr int W = 16;           // columns per CTA
+  // columns per CTA: 16, or 8 where 16 lines would not fit in shared memory
+  static constexpr int W = (P + 16 * (P + 1)) * ESZ <= 220 * 1024 ? 16 : 8;
   static constexpr int NTHR = 512;
   static constexpr int LP = P + 1;
   static constexpr int SM_ELEMS = P + W * LP;
@@ -55,7 +57,7 @@ NS3D_HD void colfast3_twiddles(cplx<LongC<T>>* tw, const cplx<T>* gtw, int tid, 
 template <typename T, int SIGN, int N1, int N2, int N3, bool PAD>
 NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
                             const cplx<LongC<T>>* tw, cplx<LongC<T>>* X) {
-  using S = ColFast3Shape<N1, N2, N3>;
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   using C = LongC<T>;
   constexpr int M = N2 * N3;
   const int c0 = bx * S::W;
@@ -98,7 +100,7 @@ NS3D_HD void colfast3_pass1(const ColArgs<T>& a, int bx, int by, int bz, int tid
 template <typename T, int SIGN, int N1, int N2, int N3>
 NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<LongC<T>>* tw,
                             cplx<LongC<T>>* X) {
-  using S = ColFast3Shape<N1, N2, N3>;
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   using C = LongC<T>;
 #pragma unroll 1
   for (int t = tid; t < S::W * N1 * N3; t += nthr) {
@@ -120,7 +122,7 @@ NS3D_HD void colfast3_pass2(int tid, int nthr, int ncol, const cplx<LongC<T>>* t
 template <typename T, int SIGN, int N1, int N2, int N3, bool TRUNC>
 NS3D_HD void colfast3_pass3(const ColArgs<T>& a, int bx, int by, int bz, int tid, int nthr,
                             const cplx<LongC<T>>* X) {
-  using S = ColFast3Shape<N1, N2, N3>;
+  using S = ColFast3Shape<N1, N2, N3, (int)sizeof(cplx<T>)>;
   using C = LongC<T>;
   const C scale = (C)a.scale;
   constexpr int M = N1 * N2;

@@ -144,6 +144,10 @@ template <typename T, int N1, int N2>
 cudaError_t zrot_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
 template <typename T, int N1, int N2>
 cudaError_t zrot_init();
+template <typename T, int N1, int N2>
+cudaError_t zadjf_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t zadjf_init();
 
 
 template <typename T>
@@ -240,6 +244,7 @@ cudaError_t kernels_init() {
     {                                                       \
       cudaError_t r = zfast_init<float, A, B>();            \
       if (r == cudaSuccess) r = zrot_init<float, A, B>();   \
+      if (r == cudaSuccess) r = zadjf_init<float, A, B>();  \
       if (r != cudaSuccess) return r;                       \
     }
     NS3D_FOR_ZFAST(NS3D_ZF_INIT)

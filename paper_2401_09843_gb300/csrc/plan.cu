@@ -462,7 +462,8 @@ namespace {
 // kernels exist (FP32 at P = 3N/2) the smallest size is taken without one.
 
 bool register_kernels_at(int N, int P, ns3d_dtype dtype) {
-  if (dtype != NS3D_F32 || 2 * P != 3 * N) return false;
+  if (2 * P != 3 * N) return false;
+  if (dtype == NS3D_F64) return zfast3_available<double>(P);   // double-single three-pass kernels
   return zfast_available<float>(P) || zfast3_available<float>(P);
 }
 

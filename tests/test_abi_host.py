@@ -387,3 +387,31 @@ def test_three_pass_z_block_1536(built):
     assert rel(out, ref) < 5e-6
     umax_ref = np.max(np.abs(u[0]) + np.abs(u[1]) + np.abs(u[2]))
     assert abs(umax.value - umax_ref) < 1e-5 * umax_ref
+
+
+@pytest.mark.parametrize("P", [48, 96])
+def test_emulated_register_adjoint_z_pass_matches_tile_block(built, P):
+    """The adjoint right-hand side's register-resident z pass (FP32; products
+    c_j = sum_l u_l S_jl of the nine fields) against the generic tile block on
+    the same random input, two x rows, emulated thread by thread; a field
+    that is zero except one line changes only that line's outputs."""
+    h, nx = P // 3, 2
+    rng = np.random.default_rng(P)
+    shape = (9, P, P, h)
+    x = ((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(P)).astype(np.complex64)
+    fast = np.zeros((3, P, P, h), np.complex64)
+    gen = np.zeros_like(fast)
+    lib = ctypes.CDLL(built.HOSTLIB)
+    rc = lib.ns3d_hostcheck_zadj(P, x.ctypes.data_as(ctypes.c_void_p), fast.ctypes.data_as(ctypes.c_void_p),
+                                 gen.ctypes.data_as(ctypes.c_void_p), nx)
+    assert rc == 0
+    assert rel(fast[:, :nx], gen[:, :nx]) < 2e-6
+    assert np.all(fast[:, nx:] == 0)
+    # independent check of one column against numpy's real FFTs
+    u = np.fft.irfft(np.concatenate([x[:, 1, 5].astype(complex), np.zeros((9, P // 2 + 1 - h))], axis=-1),
+                     n=P, axis=-1) * P
+    S = {(0, 0): u[3], (0, 1): u[4], (0, 2): u[5], (1, 1): u[6], (1, 2): u[7], (2, 2): u[8]}
+    sym = lambda j, l: S[(min(j, l), max(j, l))]
+    c = [sum(u[l] * sym(j, l) for l in range(3)) for j in range(3)]
+    ref = np.stack([np.fft.rfft(cj)[:h] for cj in c])
+    assert rel(fast[:, 1, 5], ref) < 2e-6

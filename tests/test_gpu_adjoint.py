@@ -151,3 +151,24 @@ def test_band_energy_observable(lib, dt, tol):
     with pytest.raises(B.Ns3dError):
         p.band_energy(1, 5.0, 5.0)
     p.close()
+
+
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_fp32_adjoint_step_register_z_pass(lib, N):
+    """FP32 adjoint step at the register sizes P = 3N/2 (48, 96, 192: the
+    adjoint's z pass runs register-resident there) against the oracle's
+    discrete adjoint, and the transpose identity against its tangent step."""
+    from paper_2401_09843_gb300 import binding as B
+    dt = 0.01
+    prm = S.Params(nu=0.01, eps0=1.0)
+    p = B.Plan([N], B.NS3D_F32, nu=0.01, eps0=1.0, dt_fixed=dt)
+    assert p.info(0)["P"] == 3 * N // 2
+    u = I.random_spectrum(N, seed=50 + N, k0=3.0)
+    lam = I.random_spectrum(N, seed=60 + N, k0=4.0)
+    got = p.adjoint_step(0, lam, u).cpu().numpy().astype(np.complex128)
+    ref = A.rk3_adjoint_step(u, lam, dt, prm)
+    assert rel(got, ref) < 2e-5, rel(got, ref)
+    du = I.random_spectrum(N, seed=70 + N, k0=3.0)
+    lhs = S.inner(lam, A.rk3_tangent_step(u, du, dt, prm))
+    assert abs(S.inner(got, du) - lhs) < 2e-5 * abs(lhs)
+    p.close()
