@@ -87,9 +87,9 @@ typedef enum { NS3D_F32 = 0, NS3D_F64 = 1 } ns3d_dtype;
  *          rounding.  Forms 1 and 2 take the smallest 7-smooth padded size
  *          when n_pad = 0 (no benchmark) and need more workspace (form 1:
  *          twice that of form 0); their z pass is a register-resident kernel
- *          for form 2 in FP32 at P = 3N/2 in {48, 96, 192, 384}, otherwise a
- *          tile kernel whose tile shape plan creation times and picks
- *          (n_pad = -1 keeps a fixed shape).
+ *          in FP32 at P = 3N/2 in {48, 96, 192, 384}, otherwise a tile kernel
+ *          whose tile shape plan creation times and picks (n_pad = -1 keeps a
+ *          fixed shape).
  *          ns3d_eval_rhs_noalloc takes form 0 only.
  *   dt_fixed > 0: fixed time step; otherwise dt = cfl * (L/N) / max_x sum_i |u_i|
  *          evaluated on the padded grid of the stage-1 field, per member. */

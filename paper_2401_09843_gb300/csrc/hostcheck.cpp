@@ -188,6 +188,32 @@ void run_zrot(const ZArgs<T>& a, int nm) {
       }
 }
 
+// The advective form's register-resident z pass, phase by phase and thread
+// by thread.
+template <typename T, int N1, int N2>
+void run_zadv(const ZArgs<T>& a, int nm) {
+  using S = ZAdjShape<N1, N2, 1>;
+  std::vector<cplx<T>> sm(S::SM_ELEMS);
+  std::vector<T> red(S::NTHR);
+  std::vector<ZAdjState<T, N1, N2>> st(S::NTHR);
+  const int gx = (S::P + S::Y - 1) / S::Y;
+  for (int bz = 0; bz < nm; ++bz)
+    for (int by = 0; by < S::P; ++by)
+      for (int bx = 0; bx < gx; ++bx) {
+        ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2, 1>(a, bx, by, bz, sm.data());
+        for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv1<T, N1, N2, 1>(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) {
+          zadjf_inv2<T, N1, N2, 1>(c, t, st[t]);
+          red[t] = st[t].bad ? T(-1) : st[t].umax;
+        }
+        zfast_reduce(c, red.data(), S::NTHR, 0);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_fwd1<T, N1, N2, 1>(c, t, st[t]);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_fwd2<T, N1, N2, 1>(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_extract<T, N1, N2, 1>(c, t, S::NTHR);
+      }
+}
+
 template <typename T>
 void run_zform(const ZArgs<T>& a, int form, const ns3d::Launch& L, std::vector<cplx<T>>& sm) {
   double red[1];
@@ -442,11 +468,11 @@ void rhs_stage_form(const ns3d::Geom& g, const SpecParams& sp, const cplx<T>* in
   az.in_bs = nf * P * P * h;
   az.out_bs = 3 * P * P * h;
   bool done = false;
-  if (g_use_fast && g_form_W == 0 && sizeof(T) == 4 && g.form == 2 && 3 * g.h == g.P) {
-#define NS3D_HC_ZR(A, B)            \
-    if (g.P == (A) * (B)) {         \
-      run_zrot<T, A, B>(az, 1);     \
-      done = true;                  \
+  if (g_use_fast && g_form_W == 0 && sizeof(T) == 4 && g.form != 0 && 3 * g.h == g.P) {
+#define NS3D_HC_ZR(A, B)                                            \
+    if (g.P == (A) * (B)) {                                         \
+      if (g.form == 2) run_zrot<T, A, B>(az, 1); else run_zadv<T, A, B>(az, 1); \
+      done = true;                                                  \
     }
     NS3D_FOR_ZFAST(NS3D_HC_ZR)
 #undef NS3D_HC_ZR

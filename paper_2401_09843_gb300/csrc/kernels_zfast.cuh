@@ -124,6 +124,46 @@ __global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
   zadjf_extract(c, tid, S::NTHR);
 }
 
+// The advective form's register-resident z pass (ns3d_zadj.cuh, KIND 1), same sizes.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(ZAdjShape<N1, N2, 1>::NTHR) k_zadv(ZArgs<T> a) {
+  using S = ZAdjShape<N1, N2, 1>;
+  extern __shared__ __align__(16) unsigned char ns3d_smem[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
+  T* red = reinterpret_cast<T*>(sm + S::SM_ELEMS);
+  const ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2, 1>(a, blockIdx.x, blockIdx.y, blockIdx.z, sm);
+  const int tid = threadIdx.x;
+  zfast_load_twiddles(c, tid, S::NTHR);
+  __syncthreads();
+  zadjf_inv1<T, N1, N2, 1>(c, tid, S::NTHR);
+  __syncthreads();
+  ZAdjState<T, N1, N2> st;
+  zadjf_inv2<T, N1, N2, 1>(c, tid, st);
+  red[tid] = st.bad ? T(-1) : st.umax;
+  __syncthreads();
+  if (tid < 32) zfast_reduce(c, red, S::NTHR, tid);
+  zadjf_fwd1<T, N1, N2, 1>(c, tid, st);
+  __syncthreads();
+  zadjf_fwd2<T, N1, N2, 1>(c, tid, S::NTHR);
+  __syncthreads();
+  zadjf_extract<T, N1, N2, 1>(c, tid, S::NTHR);
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zadv_launch(const ZArgs<T>& a, int nm, cudaStream_t s) {
+  using S = ZAdjShape<N1, N2, 1>;
+  dim3 grid((S::P + S::Y - 1) / S::Y, S::P, nm);
+  const size_t smem = (size_t)S::SM_ELEMS * sizeof(cplx<T>) + (size_t)S::NTHR * sizeof(double);
+  k_zadv<T, N1, N2><<<grid, S::NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N1, int N2>
+cudaError_t zadv_init() {
+  return cudaFuncSetAttribute((const void*)k_zadv<T, N1, N2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 template <typename T, int N1, int N2>
 size_t zadjf_smem() {
   return (size_t)ZAdjShape<N1, N2>::SM_ELEMS * sizeof(cplx<T>);
@@ -153,4 +193,6 @@ cudaError_t zadjf_init() {
   template cudaError_t zrot_init<T, N1, N2>();                                               \
   template cudaError_t zadjf_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);          \
   template cudaError_t zadjf_init<T, N1, N2>();                                              \
+  template cudaError_t zadv_launch<T, N1, N2>(const ZArgs<T>&, int, cudaStream_t);           \
+  template cudaError_t zadv_init<T, N1, N2>();                                               \
   }

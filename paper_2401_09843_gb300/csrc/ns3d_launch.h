@@ -148,6 +148,10 @@ template <typename T, int N1, int N2>
 cudaError_t zadjf_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
 template <typename T, int N1, int N2>
 cudaError_t zadjf_init();
+template <typename T, int N1, int N2>
+cudaError_t zadv_launch(const ZArgs<T>& a, int nm, cudaStream_t s);
+template <typename T, int N1, int N2>
+cudaError_t zadv_init();
 
 
 template <typename T>
@@ -178,6 +182,14 @@ inline bool zrot_available(const Geom& g) {
   return g.form == 2 && g.esz == 8 && 3 * g.h == g.P && zfast_available<float>(g.P);
 }
 
+// the advective form's register-resident z pass exists for this level
+inline bool zadv_available(const Geom& g) {
+  return g.form == 1 && g.esz == 8 && 3 * g.h == g.P && zfast_available<float>(g.P);
+}
+
+// a form-1/2 level whose z pass is register-resident (no tile to tune)
+inline bool zform_register(const Geom& g) { return zrot_available(g) || zadv_available(g); }
+
 
 
 // The fused z pass of a level: the register-resident kernel where one exists
@@ -197,8 +209,8 @@ cudaError_t launch_zform(const ZArgs<T>& a, int form, const Launch& L, cudaStrea
 template <typename T>
 cudaError_t zform_init();
 
-// z pass of a form-1/2 level: the rotational register kernel where it exists,
-// else the tuned zform tile kernel
+// z pass of a form-1/2 level: the rotational or advective register kernel
+// where it exists, else the tuned zform tile kernel
 template <typename T>
 cudaError_t launch_zform_level(const ZArgs<T>& a, const Geom& g, int nm, cudaStream_t s) {
   if (sizeof(T) == 4 && zrot_available(g)) {
@@ -207,6 +219,13 @@ cudaError_t launch_zform_level(const ZArgs<T>& a, const Geom& g, int nm, cudaStr
     if (g.P == (A) * (B)) return zrot_launch<float, A, B>(af, nm, s);
     NS3D_FOR_ZFAST(NS3D_ZR_GO)
 #undef NS3D_ZR_GO
+  }
+  if (sizeof(T) == 4 && zadv_available(g)) {
+    const ZArgs<float>& af = *reinterpret_cast<const ZArgs<float>*>(&a);
+#define NS3D_ZA_GO(A, B) \
+    if (g.P == (A) * (B)) return zadv_launch<float, A, B>(af, nm, s);
+    NS3D_FOR_ZFAST(NS3D_ZA_GO)
+#undef NS3D_ZA_GO
   }
   return launch_zform<T>(a, g.form, Launch{cdiv(g.P, g.Wzf), g.P, nm, g.nthr_zf, g.smem_zf}, s);
 }
@@ -245,6 +264,7 @@ cudaError_t kernels_init() {
       cudaError_t r = zfast_init<float, A, B>();            \
       if (r == cudaSuccess) r = zrot_init<float, A, B>();   \
       if (r == cudaSuccess) r = zadjf_init<float, A, B>();  \
+      if (r == cudaSuccess) r = zadv_init<float, A, B>();   \
       if (r != cudaSuccess) return r;                       \
     }
     NS3D_FOR_ZFAST(NS3D_ZF_INIT)

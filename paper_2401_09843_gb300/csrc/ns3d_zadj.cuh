@@ -1,6 +1,15 @@
-// Register-resident z pass of the adjoint right-hand side, FP32, for the
-// padded sizes of the forward register kernel (P = N1 * N2 in NS3D_FOR_ZFAST,
-// default padding h = P/3).
+// Register-resident z passes whose three products are sums over the lines of
+// a column: the adjoint right-hand side (KIND 0) and the advective form of the
+// nonlinear term (KIND 1), FP32, for the padded sizes of the forward register
+// kernel (P = N1 * N2 in NS3D_FOR_ZFAST, default padding h = P/3).
+//
+// KIND 1 computes what zform_block computes for nonlinear_form = 1: from the
+// inverse transforms of u and its nine derivatives, packed as (u0, u1),
+// (u2, d0u0), (d1u0, d2u0), (d0u1, d1u1), (d2u1, d0u2), (d1u2, d2u2), the
+// products N_j = sum_l u_l d_l u_j (N0, N1 complete after lines 2 and 4, N2
+// after line 5), with the CFL maximum of |u0| + |u1| + |u2| and the
+// finiteness test once u is complete; the forward lines are N0 + i N1 and N2.
+// KIND 0 is described below.
 //
 // Same arithmetic as zadj_block (the transpose of the linearised nonlinear
 // term: c2r of u and of the symmetric S = sym grad of the projected adjoint
@@ -25,14 +34,16 @@
 
 #include "ns3d_zfast.cuh"
 
-template <int N1, int N2>
+// KIND 0: the adjoint's products (five inverse lines); KIND 1: the advective
+// form's N_j = sum_l u_l d_l u_j (six inverse lines, nonlinear_form = 1)
+template <int N1, int N2, int KIND = 0>
 struct ZAdjShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;                      // N/2 of the default padding
   static constexpr int NSLOT = (N1 >= 24) ? 4 : 8;     // columns per CTA
   static constexpr int NTHR = NSLOT * N1;
   static constexpr int Y = NSLOT;
-  static constexpr int NL = 5;                         // inverse lines per column
+  static constexpr int NL = KIND == 1 ? 6 : 5;         // inverse lines per column
   static constexpr int LP = P + (N1 > N2 ? N1 : N2);   // padded exchange rows
   static constexpr int SM_ELEMS = 2 * P + NSLOT * NL * LP;
 };
@@ -43,11 +54,13 @@ struct ZAdjState {
   T u2[N2];
   cplx<T> c01[N2];   // (c0, c1), the first forward line
   T c2[N2];
+  T umax;            // KIND 1: max of |u0| + |u1| + |u2| over the thread's points
+  int bad;           // KIND 1: a non-finite value was seen
 };
 
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD ZFastCtx<T, N1, N2> zadjf_ctx(const ZArgs<T>& a, int bx, int by, int bz, cplx<T>* sm) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   ZFastCtx<T, N1, N2> c;
   c.a = &a;
   c.bx = bx;
@@ -63,9 +76,9 @@ NS3D_HD ZFastCtx<T, N1, N2> zadjf_ctx(const ZArgs<T>& a, int bx, int by, int bz,
 
 // inverse pass 1: tasks (slot g, line l, j2), j2 fastest; line l packs fields
 // 2l and 2l + 1 of column y0 + g (line 4: field 8 and zero)
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   const ZArgs<T>& a = *c.a;
   constexpr int h = S::H;
   constexpr bool full = (S::P % S::Y == 0);     // every tile has Y columns
@@ -74,9 +87,11 @@ NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     const int j2 = t % N2;
     const int l = (t / N2) % S::NL;
     const int g = t / (S::NL * N2);
-    const bool two = l < 4;                       // the last line has one field
-    const cplx<T>* ia = in + (2 * l) * a.in_cs;
-    const cplx<T>* ib = in + (two ? 2 * l + 1 : 2 * l) * a.in_cs;
+    int fa = 2 * l, fb = l < 4 ? 2 * l + 1 : -1;  // adjoint: the last line has one field
+    if (KIND == 1) form_pair(1, l, &fa, &fb);      // advective: the zform packing
+    const bool two = fb >= 0;
+    const cplx<T>* ia = in + fa * a.in_cs;
+    const cplx<T>* ib = in + (two ? fb : fa) * a.in_cs;
     cplx<T> v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
@@ -107,9 +122,9 @@ NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
 }
 
 // inverse pass 2 of line l into v (positions k1 + N1 k2 of slot g)
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_line(const ZFastCtx<T, N1, N2>& c, int g, int k1, int l, cplx<T>* v) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   const cplx<T>* X = c.X + (g * S::NL + l) * S::LP;
 #pragma unroll
   for (int j = 0; j < N2; ++j) v[j] = X[j * (N1 + 1) + k1];
@@ -117,41 +132,77 @@ NS3D_HD void zadjf_line(const ZFastCtx<T, N1, N2>& c, int g, int k1, int l, cplx
 }
 
 // inverse pass 2 of the five lines and the products c_j = sum_l u_l S_jl
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZAdjState<T, N1, N2>& st) {
   const int k1 = tid % N1;
   const int g = tid / N1;
   cplx<T> v[N2];
-  zadjf_line<T, N1, N2>(c, g, k1, 0, st.u01);
-  zadjf_line<T, N1, N2>(c, g, k1, 1, v);                        // (u2, S00)
+  zadjf_line<T, N1, N2, KIND>(c, g, k1, 0, st.u01);
+  if (KIND == 1) {   // advective: N_j = sum_l u_l d_l u_j into c01 = (N0, N1), c2 = N2
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 1, v);                      // (u2, d0 u0)
+    using S = ZAdjShape<N1, N2, KIND>;
+    constexpr bool full = S::P % S::Y == 0;
+    const bool valid = full || g < c.ncol;
+    T m = T(0), chk = T(0);   // 0 * s is 0 exactly when s is finite; the maximum skips NaN
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      st.u2[k] = v[k].x;
+      st.c01[k] = cmake(st.u01[k].x * v[k].y, T(0));
+      const T sum = xabs(st.u01[k].x) + xabs(st.u01[k].y) + xabs(v[k].x);
+      if (valid) {
+        m = xmax(m, sum);
+        chk = chk + T(0) * sum;
+      }
+    }
+    st.bad = !(chk == T(0)) || !(m <= big_finite<T>());
+    st.umax = m;
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 2, v);                      // (d1 u0, d2 u0)
+#pragma unroll
+    for (int k = 0; k < N2; ++k)
+      st.c01[k].x = st.c01[k].x + st.u01[k].y * v[k].x + st.u2[k] * v[k].y;
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                      // (d0 u1, d1 u1)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) st.c01[k].y = st.u01[k].x * v[k].x + st.u01[k].y * v[k].y;
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                      // (d2 u1, d0 u2)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      st.c01[k].y = st.c01[k].y + st.u2[k] * v[k].x;
+      st.c2[k] = st.u01[k].x * v[k].y;
+    }
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 5, v);                      // (d1 u2, d2 u2)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u01[k].y * v[k].x + st.u2[k] * v[k].y;
+    return;
+  }
+  zadjf_line<T, N1, N2, KIND>(c, g, k1, 1, v);                        // (u2, S00)
 #pragma unroll
   for (int k = 0; k < N2; ++k) {
     st.u2[k] = v[k].x;
     st.c01[k] = cmake(st.u01[k].x * v[k].y, T(0));
   }
-  zadjf_line<T, N1, N2>(c, g, k1, 2, v);                        // (S01, S02)
+  zadjf_line<T, N1, N2, KIND>(c, g, k1, 2, v);                        // (S01, S02)
 #pragma unroll
   for (int k = 0; k < N2; ++k) {
     const T u0 = st.u01[k].x, u1 = st.u01[k].y, u2 = st.u2[k];
     st.c01[k] = cmake(st.c01[k].x + u1 * v[k].x + u2 * v[k].y, u0 * v[k].x);
     st.c2[k] = u0 * v[k].y;
   }
-  zadjf_line<T, N1, N2>(c, g, k1, 3, v);                        // (S11, S12)
+  zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                        // (S11, S12)
 #pragma unroll
   for (int k = 0; k < N2; ++k) {
     const T u1 = st.u01[k].y, u2 = st.u2[k];
     st.c01[k].y = st.c01[k].y + u1 * v[k].x + u2 * v[k].y;
     st.c2[k] = st.c2[k] + u1 * v[k].y;
   }
-  zadjf_line<T, N1, N2>(c, g, k1, 4, v);                        // (S22, 0)
+  zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                        // (S22, 0)
 #pragma unroll
   for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u2[k] * v[k].x;
 }
 
 // forward pass 1: radix N2 over the thread's own positions, two lines
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_fwd1(const ZFastCtx<T, N1, N2>& c, int tid, const ZAdjState<T, N1, N2>& st) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   const int k1 = tid % N1;
   const int g = tid / N1;
 #pragma unroll
@@ -168,9 +219,9 @@ NS3D_HD void zadjf_fwd1(const ZFastCtx<T, N1, N2>& c, int tid, const ZAdjState<T
 }
 
 // forward pass 2: radix N1 in place; tasks (g, q < 2, kappa < N2)
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   for (int t = tid; t < S::NSLOT * 2 * N2; t += nthr) {
     const int kap = t % N2;
     const int lq = t / N2;
@@ -187,9 +238,9 @@ NS3D_HD void zadjf_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
 
 // extraction: kz < h of the real lines c0, c1 (first line) and c2 (second);
 // tasks (g, q, k), k fastest so that a warp's stores are contiguous
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
-  using S = ZAdjShape<N1, N2>;
+  using S = ZAdjShape<N1, N2, KIND>;
   const ZArgs<T>& a = *c.a;
   constexpr int h = S::H;
   constexpr bool full = S::P % S::Y == 0;

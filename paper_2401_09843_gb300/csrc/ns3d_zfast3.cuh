@@ -39,8 +39,9 @@ template <> NS3D_HD df64 big_finite<df64>() { return df64(3.4028234663852886e38f
 
 #define NS3D_FOR_ZFAST3(X) X(16, 12, 8)
 // FP64 (double-single arithmetic; the compile-time pruning of the padding
-// and truncation bands saves arithmetic): P = 192, 384, 1152
-#define NS3D_FOR_ZFAST3_F64(X) X(16, 4, 3) X(16, 4, 6) X(16, 9, 8)
+// and truncation bands saves arithmetic): P = 192, 384, 1152 (the z pass at
+// 384 as 8 x 8 x 6: 10% faster than 16 x 4 x 6 in a standalone timing)
+#define NS3D_FOR_ZFAST3_F64(X) X(16, 4, 3) X(8, 8, 6) X(16, 9, 8)
 #define NS3D_FOR_COLFAST3_F64(X) X(16, 4, 3) X(16, 4, 6) X(16, 9, 8)
 
 template <int N1, int N2, int N3>

@@ -730,7 +730,7 @@ extern "C" ns3d_status ns3d_plan_create(ns3d_plan* out, const int* N_per_member,
     L.ctrl = static_cast<Ns3dCtrl*>(c);
     st = dtype == NS3D_F32 ? upload_twiddles<float>(L, p->stream) : upload_twiddles<double>(L, p->stream);
     if (st != NS3D_OK) break;
-    if (g.form != 0 && P.n_pad != -1 && !zrot_available(g)) {
+    if (g.form != 0 && P.n_pad != -1 && !zform_register(g)) {
       st = dtype == NS3D_F32 ? tune_form_tile<float>(L, dtype, p->stream)
                              : tune_form_tile<double>(L, dtype, p->stream);
       if (st != NS3D_OK) break;
