@@ -555,7 +555,7 @@ KINDS = ["inverse_x", "inverse_y", "zpass", "forward_y", "forward_x", "spectral"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one ncu
 # capture of the same command on GB300, keyed (kind, N, dtype, members), with the profiles/
 # file that records the capture; an entry is removed when its kernel changes after the capture
-NCU_TRAFFIC = {("zpass", 256, "f32", 1): (453.12e6 + 845.53e6, "profiles/zpass_256cube_f32.md")}
+NCU_TRAFFIC = {("zpass", 256, "f32", 1): (453.16e6 + 845.25e6, "profiles/zpass_256cube_f32.md")}
 
 
 def traffic_entry(kind: str, N: int, dtype: str, members: int):
