@@ -360,21 +360,31 @@ def bench_cufft(torch, N: int = 256, steps: int = 5):
 
 
 def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
-    """Band-energy gradient (8 <= |k| < 16 at step `nsteps`, checkpoints every
-    `every` steps, fixed dt) at 128^3: wall time of one gradient, forward
-    recomputation included, against `nsteps` forward steps."""
+    """Band-energy gradient (8 <= |k| < 16 at step `nsteps`, fixed dt) at 128^3:
+    wall time of one gradient against `nsteps` forward steps, with every stage
+    state kept from the forward pass (checkpoint_every = 0: 3 nsteps states in
+    HBM, nothing recomputed) and with checkpoints every `every` steps (each
+    segment recomputed once)."""
     import ns3d_inputs as I
     out, grads = {}, {}
     for dt_name, dtype in (("f32", B.NS3D_F32), ("f64", B.NS3D_F64)):
         plan = B.Plan([N], dtype, eps0=1.0, dt_fixed=0.005)
         plan.set_initial(0, I.random_spectrum(N, seed=20240004))
         plan.grad_band_energy(0, 8.0, 16.0, 2, checkpoint_every=2)     # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        g = plan.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=every)
-        torch.cuda.synchronize()
-        tg = time.perf_counter() - t0
-        grads[dt_name] = g.to(torch.complex128)
+        r = {}
+        for mode, C in (("kept", 0), ("checkpointed", every)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = plan.grad_band_energy(0, 8.0, 16.0, nsteps, checkpoint_every=C)
+            torch.cuda.synchronize()
+            r[mode] = time.perf_counter() - t0
+            if mode == "kept":
+                grads[dt_name] = g.to(torch.complex128)
+            else:
+                d = g.to(torch.complex128) - grads[dt_name]
+                r["modes_rel_l2"] = float(torch.linalg.vector_norm(d) /
+                                          torch.linalg.vector_norm(grads[dt_name]))
+            del g
         plan.step(2)
         plan.synchronize()
         t0 = time.perf_counter()
@@ -382,11 +392,16 @@ def bench_adjoint(B, torch, N: int = 128, nsteps: int = 200, every: int = 20):
         plan.synchronize()
         tf = time.perf_counter() - t0
         plan.close()
-        out[dt_name] = {"gradient_s": tg, "forward_s": tf, "ratio": tg / tf}
+        out[dt_name] = {"gradient_s": r["kept"], "forward_s": tf, "ratio": r["kept"] / tf,
+                        "checkpointed_gradient_s": r["checkpointed"],
+                        "checkpointed_ratio": r["checkpointed"] / tf,
+                        "kept_vs_checkpointed_rel_l2": r["modes_rel_l2"]}
     d = grads["f32"] - grads["f64"]
     out["f32_gradient_rel_l2_vs_f64"] = float(torch.linalg.vector_norm(d) /
                                               torch.linalg.vector_norm(grads["f64"]))
-    return {"N": N, "steps": nsteps, "checkpoint_every": every, **out}
+    return {"N": N, "steps": nsteps, "checkpoint_every": {"kept": 0, "checkpointed": every},
+            "kept_states_GB": {"f32": 3 * nsteps * 3 * N * N * (N // 2) * 8 / 1e9,
+                               "f64": 3 * nsteps * 3 * N * N * (N // 2) * 16 / 1e9}, **out}
 
 
 def bench_mesh_refinement(B, torch, levels=(64, 128), ref_N: int = 256, members: int = 16,

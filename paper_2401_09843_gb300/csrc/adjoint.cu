@@ -196,6 +196,17 @@ ns3d_status forward_step(AdjWork<T>& w, cplx<T>* state, cudaStream_t s) {
   return NS3D_OK;
 }
 
+// the stages of one forward step from u0, each kept in its own buffer: u1 and
+// u2 (stages 1 and 2) and, unless `next` is null, u_{n+1} (stage 3)
+template <typename T>
+ns3d_status forward_stages(AdjWork<T>& w, cplx<T>* u0, cplx<T>* u1, cplx<T>* u2, cplx<T>* next,
+                           cudaStream_t s) {
+  NS3D_TRY(enqueue_rhs<T>(w.bufs(u0, u1), 1, 1, u0, u1, false, s));
+  NS3D_TRY(enqueue_rhs<T>(w.bufs(u0, u1), 2, 1, u1, u2, false, s));
+  if (next) NS3D_TRY(enqueue_rhs<T>(w.bufs(u0, u2), 3, 1, u2, next, false, s));
+  return NS3D_OK;
+}
+
 // bh <- T_N F[sum_l u_l S_jl(Leray w)] (unnormalised), left in w.A9
 template <typename T>
 ns3d_status adjoint_products(AdjWork<T>& W, const cplx<T>* u, const cplx<T>* w, cudaStream_t s) {
@@ -282,27 +293,33 @@ ns3d_status combine(AdjWork<T>& W, const cplx<T>* w, const cplx<T>* X, const cpl
   return NS3D_OK;
 }
 
+// lam_out = adjoint of one step, applied to lam3, given the step's forward
+// stage states u = u_n, u1, u2
+template <typename T>
+ns3d_status adjoint_stages(AdjWork<T>& W, const cplx<T>* u, const cplx<T>* u1, const cplx<T>* u2,
+                           const cplx<T>* lam3, cplx<T>* lam_out, cudaStream_t s) {
+  // a2 = 2/3 lam + 2/3 dt J(u2)^T lam
+  NS3D_TRY(adjoint_products<T>(W, u2, lam3, s));
+  NS3D_TRY(combine<T>(W, lam3, nullptr, nullptr, W.a2, 2.0 / 3.0, 2.0 / 3.0, 0, 0, s));
+  // a1 = 1/4 a2 + 1/4 dt J(u1)^T a2
+  NS3D_TRY(adjoint_products<T>(W, u1, W.a2, s));
+  NS3D_TRY(combine<T>(W, W.a2, nullptr, nullptr, W.a1, 0.25, 0.25, 0, 0, s));
+  // lam_n = a1 + dt J(u)^T a1 + 1/3 lam + 3/4 a2
+  NS3D_TRY(adjoint_products<T>(W, u, W.a1, s));
+  NS3D_TRY(combine<T>(W, W.a1, lam3, W.a2, lam_out, 1.0, 1.0, 1.0 / 3.0, 0.75, s));
+  return NS3D_OK;
+}
+
 // lam_out = adjoint of one step at the forward state un, applied to lam3
+// (the stages u1, u2 of the step recomputed from un)
 template <typename T>
 ns3d_status adjoint_step_c(AdjWork<T>& W, const cplx<T>* un, const cplx<T>* lam3, cplx<T>* lam_out,
                            cudaStream_t s) {
   const long long nU = W.g->nU;
   NS3D_CUDA(cudaMemcpyAsync(W.u[0], un, nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
   NS3D_CUDA(launch_ctrl_reset(W.ctrl, 1, s));
-  // recompute the stages u1, u2 of the step
-  const StageBufs b1 = W.bufs(W.u[0], W.u[1]);
-  NS3D_TRY(enqueue_rhs<T>(b1, 1, 1, W.u[0], W.u[1], false, s));
-  NS3D_TRY(enqueue_rhs<T>(b1, 2, 1, W.u[1], W.u[2], false, s));
-  // a2 = 2/3 lam + 2/3 dt J(u2)^T lam
-  NS3D_TRY(adjoint_products<T>(W, W.u[2], lam3, s));
-  NS3D_TRY(combine<T>(W, lam3, nullptr, nullptr, W.a2, 2.0 / 3.0, 2.0 / 3.0, 0, 0, s));
-  // a1 = 1/4 a2 + 1/4 dt J(u1)^T a2
-  NS3D_TRY(adjoint_products<T>(W, W.u[1], W.a2, s));
-  NS3D_TRY(combine<T>(W, W.a2, nullptr, nullptr, W.a1, 0.25, 0.25, 0, 0, s));
-  // lam_n = a1 + dt J(u)^T a1 + 1/3 lam + 3/4 a2
-  NS3D_TRY(adjoint_products<T>(W, W.u[0], W.a1, s));
-  NS3D_TRY(combine<T>(W, W.a1, lam3, W.a2, lam_out, 1.0, 1.0, 1.0 / 3.0, 0.75, s));
-  return NS3D_OK;
+  NS3D_TRY(forward_stages<T>(W, W.u[0], W.u[1], W.u[2], nullptr, s));
+  return adjoint_stages<T>(W, W.u[0], W.u[1], W.u[2], lam3, lam_out, s);
 }
 
 size_t d1_elems(int N) { return (size_t)3 * N * N * (N / 2 + 1); }
@@ -353,42 +370,59 @@ ns3d_status grad_impl(ns3d_plan p, const LevelView& L, int idx, double k_lo, dou
                       int nsteps, int C, void* grad, int on_device) {
   const double dt = plan_params(p).dt_fixed;
   if (!(dt > 0)) return NS3D_ERR_NOT_SUPPORTED;
-  if (C <= 0) C = 1;
+  // C <= 0: one segment whose stage states all come from the forward pass
+  const bool keep_all = C <= 0;
+  if (keep_all) C = nsteps > 0 ? nsteps : 1;
   cudaStream_t s = p_stream(p);
   AdjWork<T> W;
   if (!W.init(L, dt)) return NS3D_ERR_OUT_OF_MEMORY;
   const long long nU = W.g->nU;
   const int nck = (nsteps + C - 1) / C;
-  cplx<T>* ck = W.alloc((size_t)(nck > 0 ? nck : 1) * nU);   // checkpoints
-  cplx<T>* seg = W.alloc((size_t)C * nU);                     // states of one segment
+  // checkpoints (every C-th state), and the stage states u_n, u1, u2 of each
+  // step of one segment at seg + 3 i nU
+  cplx<T>* ck = keep_all ? nullptr : W.alloc((size_t)(nck > 0 ? nck : 1) * nU);
+  cplx<T>* seg = W.alloc((size_t)3 * C * nU);
   cplx<T>* state = W.alloc(nU);
   cplx<T>* lam = W.alloc(nU);
   cplx<T>* lam2 = W.alloc(nU);
   cplx<T>* staging = W.alloc(d1_elems(L.N));
-  if (!ck || !seg || !state || !lam || !lam2 || !staging) return NS3D_ERR_OUT_OF_MEMORY;
+  if ((!keep_all && !ck) || !seg || !state || !lam || !lam2 || !staging)
+    return NS3D_ERR_OUT_OF_MEMORY;
+  auto stage_buf = [&](int i, int j) { return seg + ((size_t)3 * i + j) * nU; };
   NS3D_CUDA(launch_ctrl_reset(W.ctrl, 1, s));
   NS3D_CUDA(cudaMemcpyAsync(state, static_cast<const cplx<T>*>(L.U0) + (size_t)idx * nU,
                             nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
-  for (int n = 0; n < nsteps; ++n) {
-    if (n % C == 0)
-      NS3D_CUDA(cudaMemcpyAsync(ck + (size_t)(n / C) * nU, state, nU * sizeof(cplx<T>),
-                                cudaMemcpyDeviceToDevice, s));
-    NS3D_TRY(forward_step<T>(W, state, s));
+  if (keep_all) {
+    NS3D_CUDA(cudaMemcpyAsync(stage_buf(0, 0), state, nU * sizeof(cplx<T>),
+                              cudaMemcpyDeviceToDevice, s));
+    for (int n = 0; n < nsteps; ++n)
+      NS3D_TRY(forward_stages<T>(W, stage_buf(n, 0), stage_buf(n, 1), stage_buf(n, 2),
+                                 n + 1 < nsteps ? stage_buf(n + 1, 0) : state, s));
+  } else {
+    for (int n = 0; n < nsteps; ++n) {
+      if (n % C == 0)
+        NS3D_CUDA(cudaMemcpyAsync(ck + (size_t)(n / C) * nU, state, nU * sizeof(cplx<T>),
+                                  cudaMemcpyDeviceToDevice, s));
+      NS3D_TRY(forward_step<T>(W, state, s));
+    }
   }
   // lam(T) = dJ/du(T) = u(T) on the band
   k_band<T><<<plane_grid(L.N), 256, 0, s>>>(state, lam, L.N, k_lo, k_hi);
   NS3D_CUDA(cudaGetLastError());
   for (int sgi = nck - 1; sgi >= 0; --sgi) {
     const int start = sgi * C, end = (start + C < nsteps) ? start + C : nsteps;
-    NS3D_CUDA(cudaMemcpyAsync(seg, ck + (size_t)sgi * nU, nU * sizeof(cplx<T>),
-                              cudaMemcpyDeviceToDevice, s));
-    for (int n = start + 1; n < end; ++n) {
-      cplx<T>* dst = seg + (size_t)(n - start) * nU;
-      NS3D_CUDA(cudaMemcpyAsync(dst, dst - nU, nU * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
-      NS3D_TRY(forward_step<T>(W, dst, s));
+    if (!keep_all) {
+      // recompute the segment from its checkpoint, keeping every stage state
+      NS3D_CUDA(launch_ctrl_reset(W.ctrl, 1, s));
+      NS3D_CUDA(cudaMemcpyAsync(stage_buf(0, 0), ck + (size_t)sgi * nU, nU * sizeof(cplx<T>),
+                                cudaMemcpyDeviceToDevice, s));
+      for (int i = 0; i < end - start; ++i)
+        NS3D_TRY(forward_stages<T>(W, stage_buf(i, 0), stage_buf(i, 1), stage_buf(i, 2),
+                                   i + 1 < end - start ? stage_buf(i + 1, 0) : nullptr, s));
     }
     for (int n = end - 1; n >= start; --n) {
-      NS3D_TRY(adjoint_step_c<T>(W, seg + (size_t)(n - start) * nU, lam, lam2, s));
+      const int i = n - start;
+      NS3D_TRY(adjoint_stages<T>(W, stage_buf(i, 0), stage_buf(i, 1), stage_buf(i, 2), lam, lam2, s));
       cplx<T>* t = lam;
       lam = lam2;
       lam2 = t;

@@ -33,17 +33,39 @@ def test_adjoint_step_matches_oracle(lib, N):
     p.close()
 
 
-def test_grad_band_energy_matches_oracle(lib):
+@pytest.mark.parametrize("C", [4, 1, 6, 0])
+def test_grad_band_energy_matches_oracle(lib, C):
+    """Every memory mode: segments of 4 + 2 steps, one step per checkpoint, one
+    recomputed segment, and all stage states kept from the forward pass."""
     from paper_2401_09843_gb300 import binding as B
     N, dt, n = 12, 0.04, 6
     prm = S.Params(nu=0.01, eps0=1.0)
     u0 = I.random_spectrum(N, seed=8, k0=2.5)
     p = B.Plan([N], B.NS3D_F64, nu=0.01, eps0=1.0, dt_fixed=dt)
     p.set_initial(0, u0)
-    got = p.grad_band_energy(0, 2.0, 4.0, n, checkpoint_every=4).cpu().numpy()
+    got = p.grad_band_energy(0, 2.0, 4.0, n, checkpoint_every=C).cpu().numpy()
     ref = A.grad_band_energy(u0, prm, n, dt, 2.0, 4.0, checkpoint_every=4)
     assert rel(got, ref) < 1e-11
     assert np.array_equal(p.get_state(0).cpu().numpy(), u0)     # state untouched
+    p.close()
+
+
+def test_grad_band_energy_kept_stages_fp32_match_checkpoints(lib):
+    """FP32 at a register-kernel size: the kept-stages gradient equals the
+    checkpointed one to FP32 rounding (both run the same kernels; only the
+    buffers the stage states live in differ), and zero steps give the band
+    mask itself."""
+    from paper_2401_09843_gb300 import binding as B
+    N, dt, n = 32, 0.01, 12
+    u0 = I.random_spectrum(N, seed=31, k0=4.0)
+    p = B.Plan([N], B.NS3D_F32, eps0=1.0, dt_fixed=dt)
+    p.set_initial(0, u0)
+    g0 = p.grad_band_energy(0, 4.0, 8.0, n, checkpoint_every=0).cpu().numpy()
+    g5 = p.grad_band_energy(0, 4.0, 8.0, n, checkpoint_every=5).cpu().numpy()
+    assert rel(g0, g5) < 1e-6
+    gz = p.grad_band_energy(0, 4.0, 8.0, 0, checkpoint_every=0).cpu().numpy()
+    ref = A.grad_band_energy(u0.astype(np.complex128), S.Params(eps0=1.0), 0, dt, 4.0, 8.0)
+    assert rel(gz, ref) < 1e-6
     p.close()
 
 
