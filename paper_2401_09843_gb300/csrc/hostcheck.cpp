@@ -649,7 +649,7 @@ int ns3d_hostcheck_colpass3(int sign, const void* in, void* out, int ncols) {
 // [3][nx][P][h] -> Cq-like output [6][nx][P][h]; returns the status flags and
 // the CFL maximum.
 int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
-  constexpr int P = 16 * 12 * 8, h = P / 3;
+  constexpr int P = 1536, h = P / 3;
   const std::vector<cplx<float>> tw = ns3d::make_twiddles<float>(P);
   Ns3dCtrl ctrl{};
   ZArgs<float> a{};
@@ -661,7 +661,9 @@ int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
   a.in_cs = a.out_cs = (long long)nx * P * h;
   a.xs = (long long)P * h;
   a.ctrl = &ctrl;
-  run_zfast3<float, 16, 12, 8>(a, 1, nx);
+#define NS3D_HC_Z3(A, B, C) run_zfast3<float, A, B, C>(a, 1, nx);
+  NS3D_FOR_ZFAST3(NS3D_HC_Z3)
+#undef NS3D_HC_Z3
   std::memcpy(umax, &ctrl.umax_bits, sizeof(double));
   return ctrl.status;
 }

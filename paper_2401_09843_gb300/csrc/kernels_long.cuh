@@ -133,25 +133,29 @@ cudaError_t long_init() {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
-  return zfast3_init<T, N1, N2, N3>();
+  return cudaSuccess;
 }
 
 }  // namespace ns3d
 
-#define NS3D_LONG_VARIANT(T, N1, N2, N3)                                                      \
+// the column passes of one factorisation
+#define NS3D_COLFAST3_VARIANT(T, N1, N2, N3)                                                  \
   namespace ns3d {                                                                           \
   template cudaError_t colfast3_launch<T, +1, N1, N2, N3>(const ColArgs<T>&, const Launch&,   \
                                                           cudaStream_t);                      \
   template cudaError_t colfast3_launch<T, -1, N1, N2, N3>(const ColArgs<T>&, const Launch&,   \
                                                           cudaStream_t);                      \
-  template cudaError_t zfast3_launch<T, N1, N2, N3>(const ZArgs<T>&, int, cudaStream_t);      \
   template cudaError_t long_init<T, N1, N2, N3>();                                           \
-  template cudaError_t zfast3_init<T, N1, N2, N3>();                                         \
   }
 
-// the z pass alone (a shape whose column tile would not fit in shared memory)
+// the z pass alone
 #define NS3D_ZFAST3_VARIANT(T, N1, N2, N3)                                                    \
   namespace ns3d {                                                                           \
   template cudaError_t zfast3_launch<T, N1, N2, N3>(const ZArgs<T>&, int, cudaStream_t);      \
   template cudaError_t zfast3_init<T, N1, N2, N3>();                                         \
   }
+
+// both, where the z pass and the column passes share the factorisation
+#define NS3D_LONG_VARIANT(T, N1, N2, N3) \
+  NS3D_COLFAST3_VARIANT(T, N1, N2, N3)   \
+  NS3D_ZFAST3_VARIANT(T, N1, N2, N3)

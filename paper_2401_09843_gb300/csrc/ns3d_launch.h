@@ -274,8 +274,15 @@ cudaError_t kernels_init() {
       cudaError_t r = long_init<float, A, B, C>();          \
       if (r != cudaSuccess) return r;                       \
     }
-    NS3D_FOR_ZFAST3(NS3D_LONG_INIT)
+    NS3D_FOR_COLFAST3(NS3D_LONG_INIT)
 #undef NS3D_LONG_INIT
+#define NS3D_Z3_INIT(A, B, C)                               \
+    {                                                       \
+      cudaError_t r = zfast3_init<float, A, B, C>();        \
+      if (r != cudaSuccess) return r;                       \
+    }
+    NS3D_FOR_ZFAST3(NS3D_Z3_INIT)
+#undef NS3D_Z3_INIT
 #define NS3D_XF_INIT(A, B)                                  \
     {                                                       \
       cudaError_t r = xfused_init<float, A, B>();           \

@@ -1,5 +1,5 @@
 // Fused z pass with three-pass register transforms, for long padded lines
-// P = N1 * N2 * N3 (P = 1536 = 16 * 12 * 8 at N = 1024).
+// P = N1 * N2 * N3 (P = 1536 = 24 * 8 * 8 at N = 1024).
 //
 // Same arithmetic as zfused_block and zfast (Algorithm 2 steps 2-4 along z:
 // c2r of the three velocity components with the kz padding, the six products,
@@ -37,7 +37,10 @@
 
 template <> NS3D_HD df64 big_finite<df64>() { return df64(3.4028234663852886e38f); }
 
-#define NS3D_FOR_ZFAST3(X) X(16, 12, 8)
+// FP32: P = 1536 as 24 x 8 x 8: every phase has a whole number of tasks per
+// thread (3 M = N1 N2 with M = N2 N3 = 64), and the zero band kz in [512,
+// 1024) is the whole blocks j1 = 8..15 of inverse pass 1
+#define NS3D_FOR_ZFAST3(X) X(24, 8, 8)
 // FP64 (double-single arithmetic; the compile-time pruning of the padding
 // and truncation bands saves arithmetic): P = 192, 384, 1152 (the z pass at
 // 384 as 8 x 8 x 6: 10% faster than 16 x 4 x 6 in a standalone timing)
