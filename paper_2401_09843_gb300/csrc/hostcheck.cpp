@@ -154,8 +154,10 @@ void run_zadjf(const ZArgs<T>& a, int nx) {
     for (int bx = 0; bx < gx; ++bx) {
       ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2>(a, bx, by, 0, sm.data());
       for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
-      for (int t = 0; t < S::NTHR; ++t) zadjf_inv1(c, t, S::NTHR);
-      for (int t = 0; t < S::NTHR; ++t) zadjf_inv2(c, t, st[t]);
+      for (int part = 0; part < 2; ++part) {
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv1(c, t, S::NTHR, part);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv2(c, t, st[t], part);
+      }
       for (int t = 0; t < S::NTHR; ++t) zadjf_fwd1(c, t, st[t]);
       for (int t = 0; t < S::NTHR; ++t) zadjf_fwd2(c, t, S::NTHR);
       for (int t = 0; t < S::NTHR; ++t) zadjf_extract(c, t, S::NTHR);
@@ -202,9 +204,11 @@ void run_zadv(const ZArgs<T>& a, int nm) {
       for (int bx = 0; bx < gx; ++bx) {
         ZFastCtx<T, N1, N2> c = zadjf_ctx<T, N1, N2, 1>(a, bx, by, bz, sm.data());
         for (int t = 0; t < S::NTHR; ++t) zfast_load_twiddles(c, t, S::NTHR);
-        for (int t = 0; t < S::NTHR; ++t) zadjf_inv1<T, N1, N2, 1>(c, t, S::NTHR);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv1<T, N1, N2, 1>(c, t, S::NTHR, 0);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv2<T, N1, N2, 1>(c, t, st[t], 0);
+        for (int t = 0; t < S::NTHR; ++t) zadjf_inv1<T, N1, N2, 1>(c, t, S::NTHR, 1);
         for (int t = 0; t < S::NTHR; ++t) {
-          zadjf_inv2<T, N1, N2, 1>(c, t, st[t]);
+          zadjf_inv2<T, N1, N2, 1>(c, t, st[t], 1);
           red[t] = st[t].bad ? T(-1) : st[t].umax;
         }
         zfast_reduce(c, red.data(), S::NTHR, 0);

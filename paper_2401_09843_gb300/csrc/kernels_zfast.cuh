@@ -104,7 +104,8 @@ cudaError_t zrot_init() {
 
 // The adjoint right-hand side's register-resident z pass (ns3d_zadj.cuh), same sizes.
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
+// (12 warps per SM: four blocks of 96 threads)
+__global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR, 384 / ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
   using S = ZAdjShape<N1, N2>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
@@ -112,11 +113,13 @@ __global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
   const int tid = threadIdx.x;
   zfast_load_twiddles(c, tid, S::NTHR);
   __syncthreads();
-  zadjf_inv1(c, tid, S::NTHR);
-  __syncthreads();
   ZAdjState<T, N1, N2> st;
-  zadjf_inv2(c, tid, st);
-  __syncthreads();
+  for (int part = 0; part < 2; ++part) {
+    zadjf_inv1(c, tid, S::NTHR, part);
+    __syncthreads();
+    zadjf_inv2(c, tid, st, part);
+    __syncthreads();
+  }
   zadjf_fwd1(c, tid, st);
   __syncthreads();
   zadjf_fwd2(c, tid, S::NTHR);
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(ZAdjShape<N1, N2>::NTHR) k_zadjf(ZArgs<T> a) {
 
 // The advective form's register-resident z pass (ns3d_zadj.cuh, KIND 1), same sizes.
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(ZAdjShape<N1, N2, 1>::NTHR) k_zadv(ZArgs<T> a) {
+__global__ void __launch_bounds__(ZAdjShape<N1, N2, 1>::NTHR, 384 / ZAdjShape<N1, N2, 1>::NTHR) k_zadv(ZArgs<T> a) {
   using S = ZAdjShape<N1, N2, 1>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);
@@ -135,10 +138,14 @@ __global__ void __launch_bounds__(ZAdjShape<N1, N2, 1>::NTHR) k_zadv(ZArgs<T> a)
   const int tid = threadIdx.x;
   zfast_load_twiddles(c, tid, S::NTHR);
   __syncthreads();
-  zadjf_inv1<T, N1, N2, 1>(c, tid, S::NTHR);
-  __syncthreads();
   ZAdjState<T, N1, N2> st;
-  zadjf_inv2<T, N1, N2, 1>(c, tid, st);
+  zadjf_inv1<T, N1, N2, 1>(c, tid, S::NTHR, 0);
+  __syncthreads();
+  zadjf_inv2<T, N1, N2, 1>(c, tid, st, 0);
+  __syncthreads();
+  zadjf_inv1<T, N1, N2, 1>(c, tid, S::NTHR, 1);
+  __syncthreads();
+  zadjf_inv2<T, N1, N2, 1>(c, tid, st, 1);
   red[tid] = st.bad ? T(-1) : st.umax;
   __syncthreads();
   if (tid < 32) zfast_reduce(c, red, S::NTHR, tid);

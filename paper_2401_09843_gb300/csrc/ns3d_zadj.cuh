@@ -30,6 +30,12 @@
 //   forward, pass 1   radix N2 over the same positions: c0 + i c1 and c2
 //   forward, pass 2   radix N1 in place
 //   extraction        c0, c1 from the first line, c2 from the second
+//
+// The inverse lines go through shared memory in two parts, lines 0-2 and then
+// lines 3 to NL - 1 (pass 1 of a part, barrier, pass 2 of that part, barrier),
+// so that the exchange buffer holds three lines per column instead of NL:
+// with the smaller buffer four CTAs fit on an SM instead of three (adjoint) or
+// two (advective).
 #pragma once
 
 #include "ns3d_zfast.cuh"
@@ -44,8 +50,11 @@ struct ZAdjShape {
   static constexpr int NTHR = NSLOT * N1;
   static constexpr int Y = NSLOT;
   static constexpr int NL = KIND == 1 ? 6 : 5;         // inverse lines per column
+  static constexpr int NLA = 3;                        // lines of the first part
+  static constexpr int NLR = 3;                        // exchange lines per column
   static constexpr int LP = P + (N1 > N2 ? N1 : N2);   // padded exchange rows
-  static constexpr int SM_ELEMS = 2 * P + NSLOT * NL * LP;
+  static constexpr int SM_ELEMS = 2 * P + NSLOT * NLR * LP;
+  static_assert(NL - NLA <= NLR && NLA <= NLR && NLR >= 2, "exchange lines");
 };
 
 template <typename T, int N1, int N2>
@@ -74,19 +83,28 @@ NS3D_HD ZFastCtx<T, N1, N2> zadjf_ctx(const ZArgs<T>& a, int bx, int by, int bz,
   return c;
 }
 
-// inverse pass 1: tasks (slot g, line l, j2), j2 fastest; line l packs fields
-// 2l and 2l + 1 of column y0 + g (line 4: field 8 and zero)
+// exchange row of line l of slot g (the two parts share the rows)
+template <int N1, int N2, int KIND>
+NS3D_HD int zadjf_row(int g, int l) {
+  using S = ZAdjShape<N1, N2, KIND>;
+  return (g * S::NLR + (l < S::NLA ? l : l - S::NLA)) * S::LP;
+}
+
+// inverse pass 1 of part `part` (lines 0..NLA-1, or NLA..NL-1): tasks (slot g,
+// line l, j2), j2 fastest; line l packs fields 2l and 2l + 1 of column y0 + g
+// (line 4: field 8 and zero)
 template <typename T, int N1, int N2, int KIND = 0>
-NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
+NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr, int part) {
   using S = ZAdjShape<N1, N2, KIND>;
   const ZArgs<T>& a = *c.a;
   constexpr int h = S::H;
   constexpr bool full = (S::P % S::Y == 0);     // every tile has Y columns
   const cplx<T>* in = a.in + c.bz * a.in_bs + c.by * a.xs + (long long)c.y0 * h;
-  for (int t = tid; t < S::NSLOT * S::NL * N2; t += nthr) {
+  const int l0 = part ? S::NLA : 0, nl = part ? S::NL - S::NLA : S::NLA;
+  for (int t = tid; t < S::NSLOT * nl * N2; t += nthr) {
     const int j2 = t % N2;
-    const int l = (t / N2) % S::NL;
-    const int g = t / (S::NL * N2);
+    const int l = l0 + (t / N2) % nl;
+    const int g = t / (nl * N2);
     int fa = 2 * l, fb = l < 4 ? 2 * l + 1 : -1;  // adjoint: the last line has one field
     if (KIND == 1) form_pair(1, l, &fa, &fb);      // advective: the zform packing
     const bool two = fb >= 0;
@@ -114,7 +132,7 @@ NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
       }
     }
     Dft<N1, +1>::run(v);
-    cplx<T>* X = c.X + (g * S::NL + l) * S::LP;
+    cplx<T>* X = c.X + zadjf_row<N1, N2, KIND>(g, l);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
       X[j2 * (N1 + 1) + k1] = k1 == 0 ? v[k1] : v[k1] * c.twi[k1 * N2 + j2];
@@ -124,19 +142,46 @@ NS3D_HD void zadjf_inv1(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
 // inverse pass 2 of line l into v (positions k1 + N1 k2 of slot g)
 template <typename T, int N1, int N2, int KIND = 0>
 NS3D_HD void zadjf_line(const ZFastCtx<T, N1, N2>& c, int g, int k1, int l, cplx<T>* v) {
-  using S = ZAdjShape<N1, N2, KIND>;
-  const cplx<T>* X = c.X + (g * S::NL + l) * S::LP;
+  const cplx<T>* X = c.X + zadjf_row<N1, N2, KIND>(g, l);
 #pragma unroll
   for (int j = 0; j < N2; ++j) v[j] = X[j * (N1 + 1) + k1];
   Dft<N2, +1>::run(v);
 }
 
-// inverse pass 2 of the five lines and the products c_j = sum_l u_l S_jl
+// inverse pass 2 of the lines of part `part` and the products c_j = sum_l u_l S_jl
 template <typename T, int N1, int N2, int KIND = 0>
-NS3D_HD void zadjf_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZAdjState<T, N1, N2>& st) {
+NS3D_HD void zadjf_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZAdjState<T, N1, N2>& st, int part) {
   const int k1 = tid % N1;
   const int g = tid / N1;
   cplx<T> v[N2];
+  if (KIND == 1 && part == 1) {
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                      // (d0 u1, d1 u1)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) st.c01[k].y = st.u01[k].x * v[k].x + st.u01[k].y * v[k].y;
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                      // (d2 u1, d0 u2)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      st.c01[k].y = st.c01[k].y + st.u2[k] * v[k].x;
+      st.c2[k] = st.u01[k].x * v[k].y;
+    }
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 5, v);                      // (d1 u2, d2 u2)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u01[k].y * v[k].x + st.u2[k] * v[k].y;
+    return;
+  }
+  if (KIND == 0 && part == 1) {
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                      // (S11, S12)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) {
+      const T u1 = st.u01[k].y, u2 = st.u2[k];
+      st.c01[k].y = st.c01[k].y + u1 * v[k].x + u2 * v[k].y;
+      st.c2[k] = st.c2[k] + u1 * v[k].y;
+    }
+    zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                      // (S22, 0)
+#pragma unroll
+    for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u2[k] * v[k].x;
+    return;
+  }
   zadjf_line<T, N1, N2, KIND>(c, g, k1, 0, st.u01);
   if (KIND == 1) {   // advective: N_j = sum_l u_l d_l u_j into c01 = (N0, N1), c2 = N2
     zadjf_line<T, N1, N2, KIND>(c, g, k1, 1, v);                      // (u2, d0 u0)
@@ -160,18 +205,6 @@ NS3D_HD void zadjf_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZAdjState<T, N1, 
 #pragma unroll
     for (int k = 0; k < N2; ++k)
       st.c01[k].x = st.c01[k].x + st.u01[k].y * v[k].x + st.u2[k] * v[k].y;
-    zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                      // (d0 u1, d1 u1)
-#pragma unroll
-    for (int k = 0; k < N2; ++k) st.c01[k].y = st.u01[k].x * v[k].x + st.u01[k].y * v[k].y;
-    zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                      // (d2 u1, d0 u2)
-#pragma unroll
-    for (int k = 0; k < N2; ++k) {
-      st.c01[k].y = st.c01[k].y + st.u2[k] * v[k].x;
-      st.c2[k] = st.u01[k].x * v[k].y;
-    }
-    zadjf_line<T, N1, N2, KIND>(c, g, k1, 5, v);                      // (d1 u2, d2 u2)
-#pragma unroll
-    for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u01[k].y * v[k].x + st.u2[k] * v[k].y;
     return;
   }
   zadjf_line<T, N1, N2, KIND>(c, g, k1, 1, v);                        // (u2, S00)
@@ -187,16 +220,6 @@ NS3D_HD void zadjf_inv2(const ZFastCtx<T, N1, N2>& c, int tid, ZAdjState<T, N1, 
     st.c01[k] = cmake(st.c01[k].x + u1 * v[k].x + u2 * v[k].y, u0 * v[k].x);
     st.c2[k] = u0 * v[k].y;
   }
-  zadjf_line<T, N1, N2, KIND>(c, g, k1, 3, v);                        // (S11, S12)
-#pragma unroll
-  for (int k = 0; k < N2; ++k) {
-    const T u1 = st.u01[k].y, u2 = st.u2[k];
-    st.c01[k].y = st.c01[k].y + u1 * v[k].x + u2 * v[k].y;
-    st.c2[k] = st.c2[k] + u1 * v[k].y;
-  }
-  zadjf_line<T, N1, N2, KIND>(c, g, k1, 4, v);                        // (S22, 0)
-#pragma unroll
-  for (int k = 0; k < N2; ++k) st.c2[k] = st.c2[k] + st.u2[k] * v[k].x;
 }
 
 // forward pass 1: radix N2 over the thread's own positions, two lines
@@ -211,7 +234,7 @@ NS3D_HD void zadjf_fwd1(const ZFastCtx<T, N1, N2>& c, int tid, const ZAdjState<T
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) v[k2] = q == 0 ? st.c01[k2] : cmake(st.c2[k2], T(0));
     Dft<N2, -1>::run(v);
-    cplx<T>* X = c.X + (g * S::NL + q) * S::LP;
+    cplx<T>* X = c.X + (g * S::NLR + q) * S::LP;
 #pragma unroll
     for (int k = 0; k < N2; ++k)
       X[k1 * (N2 + 1) + k] = k == 0 ? v[k] : v[k] * c.twf[k * N1 + k1];
@@ -225,7 +248,7 @@ NS3D_HD void zadjf_fwd2(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
   for (int t = tid; t < S::NSLOT * 2 * N2; t += nthr) {
     const int kap = t % N2;
     const int lq = t / N2;
-    cplx<T>* X = c.X + ((lq >> 1) * S::NL + (lq & 1)) * S::LP;
+    cplx<T>* X = c.X + ((lq >> 1) * S::NLR + (lq & 1)) * S::LP;
     cplx<T> v[N1];
 #pragma unroll
     for (int q = 0; q < N1; ++q) v[q] = X[q * (N2 + 1) + kap];
@@ -250,7 +273,7 @@ NS3D_HD void zadjf_extract(const ZFastCtx<T, N1, N2>& c, int tid, int nthr) {
     const int lq = t / h;
     const int g = lq >> 1, q = lq & 1;
     if (!full && g >= c.ncol) continue;
-    const cplx<T>* X = c.X + (g * S::NL + q) * S::LP;
+    const cplx<T>* X = c.X + (g * S::NLR + q) * S::LP;
     const cplx<T> zk = X[zfast_fpos<N1, N2>(k)];
     const cplx<T> zm = cconj(X[zfast_fpos<N1, N2>(k == 0 ? 0 : S::P - k)]);
     const cplx<T> s = zk + zm;
