@@ -9,8 +9,8 @@
 namespace ns3d {
 
 template <typename T, int N1, int N2>
-// blocks per SM: 12 warps in all (the register-resident state caps residency)
-__global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, 384 / ZFastShape<N1, N2>::NTHR) k_zfast(ZArgs<T> a) {
+// blocks per SM as ZFastShape::MINB (the register-resident state caps residency)
+__global__ void __launch_bounds__(ZFastShape<N1, N2>::NTHR, ZFastShape<N1, N2>::MINB) k_zfast(ZArgs<T> a) {
   using S = ZFastShape<N1, N2>;
   extern __shared__ __align__(16) unsigned char ns3d_smem[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(ns3d_smem);

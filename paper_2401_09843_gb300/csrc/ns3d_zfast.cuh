@@ -46,8 +46,15 @@ struct ZFastShape {
   static constexpr int NTHR = NPAIR * N1;
   static constexpr int Y = 2 * NPAIR;                 // columns per CTA
   // Exchange rows are padded by one element so that the strided pass stores
-  // (stride N1 + 1 or N2 + 1 across threads) hit distinct shared-memory banks.
-  static constexpr int LP = P + (N1 > N2 ? N1 : N2);
+  // (stride N1 + 1 or N2 + 1 across threads) hit distinct shared-memory banks,
+  // and lines start 8 elements (mod 16) apart, so that where a half-warp spans
+  // two lines (N2 = 8: inverse pass 1 and forward pass 2) their rows fall in
+  // the other half of the banks.
+  static constexpr int LP0 = P + (N1 > N2 ? N1 : N2);
+  static constexpr int LP = LP0 + (24 - LP0 % 16) % 16;
+  // blocks per SM the registers are capped for: 12 warps at N1 >= 24 (the
+  // 168-register state), 18 warps at N2 = 8 (a 2 x 8 complex state per line)
+  static constexpr int MINB = N1 >= 24 ? 4 : (N2 <= 8 ? 3 : 2);
   // shared memory in complex elements: two twiddle tables + exchange [NPAIR][3][LP]
   // (followed by NTHR reduction slots of T)
   static constexpr int SM_ELEMS = 2 * P + NPAIR * 3 * LP;
