@@ -8,8 +8,8 @@
 // shared memory:
 //
 //   pass 1  task (column c, j2 < N2): radix N1 over x[N2 j1 + j2] loaded from
-//           global memory (column-fast: a warp reads 16 adjacent columns of a
-//           row), twiddle w_P^(j2 k1), store D[c][j2 N1 + k1]
+//           global memory (column-fast: a warp reads 16 or 32 adjacent columns
+//           of a row), twiddle w_P^(j2 k1), store D[c][j2 N1 + k1]
 //   pass 2  task (c, k1 < N1): radix N2 over D[c][j N1 + k1], result
 //           X[k1 + N1 k2] stored to global memory
 //
@@ -27,10 +27,14 @@ template <int N1, int N2>
 struct ColFastShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;        // N/2 of the default padding P = 3N/2
-  static constexpr int W = 16;           // columns per CTA
+  // P = 96 (12 x 8): 32 columns and 128 threads, so that both passes have a
+  // whole number of tasks per thread (2 and 3) and a warp reads 256 contiguous
+  // bytes of a row; otherwise 16 columns
+  static constexpr bool WIDE = N1 == 12 && N2 == 8;
+  static constexpr int W = WIDE ? 32 : 16;   // columns per CTA
   // one pass-2 task per thread at radix 24 (36 warps per SM), else 256 (32 warps)
-  static constexpr int NTHR = N1 >= 24 ? 384 : 256;
-  static constexpr int MINB = N1 >= 24 ? 3 : 4;
+  static constexpr int NTHR = WIDE ? 128 : (N1 >= 24 ? 384 : 256);
+  static constexpr int MINB = WIDE ? 8 : (N1 >= 24 ? 3 : 4);
   static constexpr int LP = P + 1;
   static constexpr int SM_ELEMS = P + W * LP;
 };
