@@ -14,9 +14,16 @@
 
 namespace ns3d {
 
+// blocks per SM the registers are capped for: 12 warps, or 18 at P = 96 (96
+// registers; 149 uncapped allowed four blocks of three warps)
+template <int N1, int N2>
+constexpr int xfused_minb() {
+  return (N1 == 12 && N2 == 8) ? 6
+                               : (XFusedShape<N1, N2>::NTHR <= 192 ? 384 / XFusedShape<N1, N2>::NTHR : 1);
+}
+
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR,
-                                  XFusedShape<N1, N2>::NTHR <= 192 ? 384 / XFusedShape<N1, N2>::NTHR : 1)
+__global__ void __launch_bounds__(XFusedShape<N1, N2>::NTHR, xfused_minb<N1, N2>())
     k_xfused(const XFusedArgs<T> a, const __grid_constant__ XFusedMaps maps) {
   using S = XFusedShape<N1, N2>;
   extern __shared__ __align__(128) unsigned char ns3d_smem[];
