@@ -42,7 +42,9 @@ template <int N1, int N2>
 struct ZFastShape {
   static constexpr int P = N1 * N2;
   static constexpr int H = P / 3;                     // N/2 of the default padding P = 3N/2
-  static constexpr int NPAIR = (N1 >= 24) ? 4 : 16;   // pairs per CTA
+  // pairs per CTA: 96-thread blocks where N2 = 16 (four blocks of 3 warps per SM
+  // beat two of 6 at the same residency), else 16
+  static constexpr int NPAIR = N2 == 16 ? 96 / N1 : 16;
   static constexpr int NTHR = NPAIR * N1;
   static constexpr int Y = 2 * NPAIR;                 // columns per CTA
   // Exchange rows are padded by one element so that the strided pass stores
@@ -52,9 +54,9 @@ struct ZFastShape {
   // the other half of the banks.
   static constexpr int LP0 = P + (N1 > N2 ? N1 : N2);
   static constexpr int LP = LP0 + (24 - LP0 % 16) % 16;
-  // blocks per SM the registers are capped for: 12 warps at N1 >= 24 (the
+  // blocks per SM the registers are capped for: 12 warps at N2 = 16 (the
   // 168-register state), 18 warps at N2 = 8 (a 2 x 8 complex state per line)
-  static constexpr int MINB = N1 >= 24 ? 4 : (N2 <= 8 ? 3 : 2);
+  static constexpr int MINB = N2 == 16 ? 4 : 3;
   // shared memory in complex elements: two twiddle tables + exchange [NPAIR][3][LP]
   // (followed by NTHR reduction slots of T)
   static constexpr int SM_ELEMS = 2 * P + NPAIR * 3 * LP;
