@@ -346,9 +346,8 @@ ns3d_status ns3d_step_timed(ns3d_plan plan, int nsteps, double t_end, double* ke
  * 7-smooth P >= 3N/2, and a given P with a prime factor above 7 returns
  * NS3D_ERR_NOT_SUPPORTED (as ns3d_plan_create does).  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) and
- * keeps it for the life of the process, so that call should come before any
- * stream capture, and after a cudaDeviceReset of that device this entry point
- * must not be called again.  All calls share the array and it keeps the last
+ * keeps it for the life of the process; after a cudaDeviceReset of that
+ * device this entry point must not be called again.  All calls share the array and it keeps the last
  * call's contents: calls that overlap on the GPU race; order them on one
  * stream. */
 ns3d_status ns3d_eval_rhs_noalloc(int N, ns3d_dtype dtype, const ns3d_params* p,

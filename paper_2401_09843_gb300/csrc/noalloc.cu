@@ -33,8 +33,8 @@ constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of the array, looked up once per device (by the first call
-// on that device, which should therefore come before any stream capture) and
-// kept for the life of the process: a cudaDeviceReset of that device
+// on that device) and kept for the life of the process: a cudaDeviceReset of
+// that device
 // invalidates it, after which this entry point must not be called again.  In
 // host code the name g_noalloc_scratch is only a host-side stand-in, never a
 // device address.
