@@ -34,10 +34,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the array, looked up once per device (by the first call
 // on that device) and kept for the life of the process: a cudaDeviceReset of
-// that device
-// invalidates it, after which this entry point must not be called again.  In
-// host code the name g_noalloc_scratch is only a host-side stand-in, never a
-// device address.
+// that device invalidates it, after which this entry point must not be called
+// again.  In host code the name g_noalloc_scratch is only a host-side
+// stand-in, never a device address.
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
