@@ -672,6 +672,36 @@ int ns3d_hostcheck_zpass3(const void* in, void* out, int nx, double* umax) {
   return ctrl.status;
 }
 
+// The FP64 three-pass z pass (double-single arithmetic) at a padded size P of
+// NS3D_FOR_ZFAST3_F64 on rows x < nx of a [3][nx][P][h] complex128 array into
+// [6][nx][P][h]; returns the status flags (-1: no kernel at P) and the CFL
+// maximum.
+int ns3d_hostcheck_zpass3_f64(int P, const void* in, void* out, int nx, double* umax) {
+  const int h = P / 3;
+  const std::vector<cplx<double>> tw = ns3d::make_twiddles<double>(P);
+  Ns3dCtrl ctrl{};
+  ZArgs<double> a{};
+  a.in = static_cast<const cplx<double>*>(in);
+  a.out = static_cast<cplx<double>*>(out);
+  a.tw = tw.data();
+  a.P = P;
+  a.h = h;
+  a.in_cs = a.out_cs = (long long)nx * P * h;
+  a.xs = (long long)P * h;
+  a.ctrl = &ctrl;
+  bool done = false;
+#define NS3D_HC_Z3D(A, B, C)                 \
+  if (P == (A) * (B) * (C)) {                \
+    run_zfast3<double, A, B, C>(a, 1, nx);   \
+    done = true;                             \
+  }
+  NS3D_FOR_ZFAST3_F64(NS3D_HC_Z3D)
+#undef NS3D_HC_Z3D
+  if (!done) return -1;
+  std::memcpy(umax, &ctrl.umax_bits, sizeof(double));
+  return ctrl.status;
+}
+
 // The adjoint z pass on x rows < nx of a [9][P][P][h] complex64 array: the
 // register-resident kernel into out_fast and the generic tile block into
 // out_generic (both [3][P][P][h]).  P must be a register size (48, 96, 192,

@@ -43,8 +43,10 @@ template <> NS3D_HD df64 big_finite<df64>() { return df64(3.4028234663852886e38f
 #define NS3D_FOR_ZFAST3(X) X(24, 8, 8)
 // FP64 (double-single arithmetic; the compile-time pruning of the padding
 // and truncation bands saves arithmetic): P = 192, 384, 1152 (the z pass at
-// 384 as 8 x 8 x 6: 10% faster than 16 x 4 x 6 in a standalone timing)
-#define NS3D_FOR_ZFAST3_F64(X) X(16, 4, 3) X(8, 8, 6) X(16, 9, 8)
+// 384 as 8 x 8 x 6: 10% faster than 16 x 4 x 6 in a standalone timing; at
+// 1152 as 12 x 12 x 8: 2 tasks per thread in every phase, and the zero band
+// kz in [384, 768) is the whole pass-1 blocks j1 = 4..7)
+#define NS3D_FOR_ZFAST3_F64(X) X(16, 4, 3) X(8, 8, 6) X(12, 12, 8)
 #define NS3D_FOR_COLFAST3_F64(X) X(16, 4, 3) X(16, 4, 6) X(16, 9, 8)
 
 template <int N1, int N2, int N3>

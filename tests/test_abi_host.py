@@ -389,6 +389,32 @@ def test_three_pass_z_block_1536(built):
     assert abs(umax.value - umax_ref) < 1e-5 * umax_ref
 
 
+@pytest.mark.parametrize("P,nx", [(384, 2), (1152, 1)])
+def test_three_pass_z_block_fp64(built, P, nx):
+    """The FP64 three-pass z pass (double-single arithmetic) at the padded sizes
+    of the 256^3 and 768^3 FP64 workloads on a few x rows of random input,
+    emulated: against numpy's FP64 real FFTs at the FP64 tolerance, and the
+    CFL maximum."""
+    h = P // 3
+    rng = np.random.default_rng(P + 7)
+    shape = (3, nx, P, h)
+    bq = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(P)
+    out = np.zeros((6, nx, P, h), np.complex128)
+    umax = ctypes.c_double()
+    lib = ctypes.CDLL(built.HOSTLIB)
+    rc = lib.ns3d_hostcheck_zpass3_f64(P, bq.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                       nx, ctypes.byref(umax))
+    assert rc == 0
+    spec = np.zeros((3, nx, P, P // 2 + 1), complex)
+    spec[..., :h] = bq
+    u = np.fft.irfft(spec, n=P, axis=-1) * P          # ignores Im of kz = 0
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    ref = np.stack([np.fft.rfft(u[j] * u[l], axis=-1)[..., :h] for j, l in pairs])
+    assert rel(out, ref) < 1e-12, rel(out, ref)
+    umax_ref = np.max(np.abs(u[0]) + np.abs(u[1]) + np.abs(u[2]))
+    assert abs(umax.value - umax_ref) < 1e-6 * umax_ref
+
+
 @pytest.mark.parametrize("P", [48, 96])
 def test_emulated_register_adjoint_z_pass_matches_tile_block(built, P):
     """The adjoint right-hand side's register-resident z pass (FP32; products
