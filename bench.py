@@ -573,6 +573,13 @@ KINDS = ["inverse_x", "inverse_y", "zpass", "forward_y", "forward_x", "spectral"
 NCU_TRAFFIC = {("zpass", 256, "f32", 1): (453.16e6 + 845.25e6, "profiles/zpass_256cube_f32.md")}
 
 
+def window_sizes(steps: int, n: int = 5, min_steps: int = 20):
+    """The timed steps split into n consecutive windows of at least min_steps
+    each (one window when there are too few steps); the sizes sum to steps."""
+    n = max(1, min(n, steps // min_steps))
+    return [steps // n + (1 if i < steps % n else 0) for i in range(n)]
+
+
 def traffic_entry(kind: str, N: int, dtype: str, members: int):
     """(bytes, source) of the ncu capture for this kernel and workload, or (None, None)."""
     return NCU_TRAFFIC.get((kind, N, dtype, members), (None, None))
@@ -790,14 +797,21 @@ def main():
     barrier()
     clocks.start()
     time.sleep(0.25)
+    # the K steps in consecutive windows, an event between windows (ns3d_step
+    # only enqueues graph replays, so the windows run back to back)
+    wins = window_sizes(args.steps)
+    wev = [torch.cuda.Event(enable_timing=True) for _ in range(len(wins) - 1)]
     e0.record(stream)
-    plan.step(args.steps)
-    e1.record(stream)
+    for i, k in enumerate(wins):
+        plan.step(k)
+        (wev[i] if i < len(wev) else e1).record(stream)
     torch.cuda.synchronize()
     time.sleep(0.1)
     ck = clocks.stop()
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    bounds = [e0] + wev + [e1]
+    win_ms = [bounds[i].elapsed_time(bounds[i + 1]) / k for i, k in enumerate(wins)]
     status_ok = True
     try:
         plan.synchronize()
@@ -907,6 +921,8 @@ def main():
                      "bytes_per_launch": kb[kinds[dom]],
                      "traffic": traffic_entry(kinds[dom], N, args.dtype, M)[0],
                      "traffic_source": traffic_entry(kinds[dom], N, args.dtype, M)[1]},
+        "windows": {"steps": wins, "ms_per_step": win_ms,
+                    "median_ms_per_step": float(statistics.median(win_ms))},
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved_GBps": step_bytes / (ms / args.steps * 1e-3) / 1e9,
                           "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak},

@@ -95,3 +95,15 @@ def test_fp64_roofline_model():
     assert abs(r["achieved"] - f * 29 / 3 / 0.06 / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / 40.27392) < 1e-15
     assert abs(r["fp64_equivalent_TFLOPs"] - f / 0.06 / 1e12) < 1e-12
+
+
+def test_window_sizes_cover_the_timed_steps():
+    """The timed region's windows: five of at least 20 steps where there are
+    enough, fewer otherwise, one for short runs; they sum to the step count."""
+    assert bench.window_sizes(300) == [60] * 5
+    assert bench.window_sizes(101) == [21, 20, 20, 20, 20]
+    assert bench.window_sizes(99) == [25, 25, 25, 24]
+    assert bench.window_sizes(30) == [30] and bench.window_sizes(1) == [1]
+    for k in range(1, 400):
+        w = bench.window_sizes(k)
+        assert sum(w) == k and (len(w) == 1 or min(w) >= 20) and len(w) <= 5
